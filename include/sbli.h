@@ -1,0 +1,154 @@
+/*
+ * sbli.h -- C ABI of the GB300 (sm_103a) fused Navier-Stokes RHS + RK3 stage.
+ *
+ * The operation is the residual R(Q) of the non-dimensional compressible
+ * Navier-Stokes equations (Jammy, Jacobs, Lusher & Sandham, arXiv:1709.09713,
+ * §2, Eqs. 1-5) discretised by the fourth-order central stencils of Eqs. 6-7
+ * on a periodic grid, advanced by the three-stage low-storage Runge-Kutta
+ * scheme of §2.2 (Eq. 8, Fig. 1), on the Taylor-Green vortex of §4.
+ *
+ * Conventions for every call:
+ *  - Every function returns an int status (enum sbli_status).  Nothing aborts
+ *    the process; on failure sbli_last_error() returns a message (per host
+ *    thread) and the grid is left as it was before the call.
+ *  - Grids are n0 x n1 x n2 points on [0, 2*pi*L)^3, x_i = i*h_i,
+ *    h_i = 2*pi*L/n_i, periodic in every direction; each n_i >= 5 (the
+ *    5-point stencils of Eqs. 6-7).  Fields are stored x0-fastest
+ *    (index i + n0*(j + n1*k)), five consecutive fields per state in the
+ *    order (rho, rho*u0, rho*u1, rho*u2, rho*E).
+ *  - Device memory is owned by the caller (e.g. PyTorch): the library never
+ *    allocates or frees device memory.  It carves the caller's workspace.
+ *  - Work is enqueued on the CUDA stream given at creation; the library does
+ *    not synchronise except in calls that return host scalars or copy to or
+ *    from host memory (stated per call).
+ *  - Precision SBLI_FP64: every value stored and computed in IEEE binary64.
+ *    Precision SBLI_FP32: stage fields stored and the residual computed in
+ *    binary32; the Runge-Kutta accumulator (the n+1 level of Fig. 1) and
+ *    the state between steps are binary64; kinetic-energy and enstrophy sums
+ *    are binary64.  Both store the state as deviations from the uniform
+ *    reference state (rho = 1, u = 0, p = 1/(gamma M^2)); the
+ *    get/set calls convert to and from the plain conserved variables.
+ *  - Variant SBLI_FUSED evaluates every derivative on the fly and writes the
+ *    stage update in the same kernel (the "store none" class of §2.5, with
+ *    the RK update of Fig. 1 fused in).  Variant SBLI_STORE_ALL stores each
+ *    derivative in its own array first (the BL algorithm of §2.3.1).
+ */
+#ifndef SBLI_H
+#define SBLI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBLI_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define SBLI_API __attribute__((visibility("default")))
+#else
+#define SBLI_API
+#endif
+
+enum sbli_status {
+  SBLI_OK = 0,
+  SBLI_EINVAL = 1,       /* bad argument: size, pointer, alignment, stage order */
+  SBLI_ENOMEM = 2,       /* the caller's workspace is smaller than required */
+  SBLI_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  SBLI_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  SBLI_EUNSUPPORTED = 5  /* precision/variant combination not provided */
+};
+
+enum sbli_precision { SBLI_FP64 = 0, SBLI_FP32 = 1 };
+enum sbli_variant { SBLI_FUSED = 0, SBLI_STORE_ALL = 1 };
+
+/* Physical parameters (§2 Eqs. 1-5, §4): Re may be +INFINITY, which removes
+ * the viscous and heat-flux terms. */
+typedef struct {
+  double Re;    /* Reynolds number, > 0 */
+  double Mach;  /* reference Mach number M, > 0 */
+  double Pr;    /* Prandtl number, > 0 */
+  double gamma; /* ratio of specific heats, > 1 */
+  double L;     /* domain edge is 2*pi*L, > 0 */
+} sbli_params;
+
+typedef struct sbli_grid sbli_grid;
+
+/* ABI version the library was built with (SBLI_ABI_VERSION). */
+SBLI_API int sbli_abi_version(void);
+
+/* Bytes of device workspace a grid needs (state registers, stage fields and
+ * scratch).  Returns SBLI_EINVAL for n_i < 5 or unknown precision/variant. */
+SBLI_API int sbli_workspace_bytes(int n0, int n1, int n2, int precision, int variant, size_t* bytes);
+
+/* Create a grid over a caller-owned device workspace of at least
+ * sbli_workspace_bytes() bytes, 256-byte aligned.  stream is a cudaStream_t
+ * (NULL = legacy default stream).  The workspace must stay allocated until
+ * sbli_destroy_grid.  The state is undefined until sbli_init_tgv or
+ * sbli_set_state. */
+SBLI_API int sbli_create_grid(sbli_grid** out, int n0, int n1, int n2, int precision, int variant,
+                     const sbli_params* params, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Release the handle (not the workspace).  Waits for the grid's stream. */
+SBLI_API int sbli_destroy_grid(sbli_grid* g);
+
+/* Taylor-Green initial field of §4 (Eqs. 9-12), velocity amplitude A
+ * (A = 1 is the paper's), density from T = 1 (rho = gamma M^2 p, Eq. 5) and
+ * rho*E from Eq. 4.  Asynchronous. */
+SBLI_API int sbli_init_tgv(sbli_grid* g, double amplitude);
+
+/* Copy the state in or out as 5*n0*n1*n2 binary64 plain conserved variables.
+ * q_is_host != 0: q is host memory (ideally pinned); the call copies through
+ * the grid's stream and returns after the copy completed.  q_is_host == 0: q
+ * is device memory, asynchronous.  Fails with SBLI_EINVAL between the stages
+ * of a time step. */
+SBLI_API int sbli_set_state(sbli_grid* g, const double* q, int q_is_host);
+SBLI_API int sbli_get_state(sbli_grid* g, double* q, int q_is_host);
+
+/* Between the stages of a step (after stage 0 or 1): copy out the next
+ * stage's input field Q_k and the accumulator Q_acc as 5*n0*n1*n2 binary64
+ * plain conserved variables (binary32 stage fields are widened).  For
+ * verifying single stages.  Either pointer may be NULL.  q_is_host as in
+ * sbli_get_state (host copies synchronise). */
+SBLI_API int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host);
+
+/* R(Q) of the current state (Eqs. 1-3 with Eqs. 4-7) into r_dev, a device
+ * array of 5*n0*n1*n2 binary64, same field order as the state.  For SBLI_FP32
+ * grids the residual is computed in binary32 and widened.  Asynchronous. */
+SBLI_API int sbli_rhs(sbli_grid* g, double* r_dev);
+
+/* One Runge-Kutta stage k = 0, 1, 2 of the current step (§2.2, Fig. 1), in
+ * two-register form with stage coefficients a = (2/3, 5/12, 3/5) and
+ * accumulator coefficients b = (1/4, 3/20, 3/5):
+ *     R = R(Q_k);  Q_{k+1} = Q_acc + a_k dt R;  Q_acc = Q_acc + b_k dt R,
+ * Q_acc = Q^n before stage 0 and Q^{n+1} = Q_acc after stage 2.  Stages
+ * must be called in order 0, 1, 2 (else SBLI_EINVAL); dt > 0.  Asynchronous. */
+SBLI_API int sbli_rk_stage(sbli_grid* g, int stage, double dt);
+
+/* nsteps complete time steps (3*nsteps stages), launched as a captured CUDA
+ * graph.  Must start at a step boundary.  Asynchronous. */
+SBLI_API int sbli_step_n(sbli_grid* g, int nsteps, double dt);
+
+/* As sbli_step_n, and writes the volume-averaged kinetic energy and enstrophy
+ * of Q^n before each step s into ke_hist_dev[2*s], ke_hist_dev[2*s+1]
+ * (device memory, 2*nsteps binary64).  Fused variant only. Asynchronous. */
+SBLI_API int sbli_step_n_history(sbli_grid* g, int nsteps, double dt, double* ke_hist_dev);
+
+/* Volume averages of the current state, accumulated in binary64:
+ *   ke = <rho |u|^2 / 2>,  enstrophy = <rho |omega|^2 / 2>,  omega = curl u
+ * with Eq. 6 derivatives.  Synchronises the grid's stream. */
+SBLI_API int sbli_kinetic_energy(sbli_grid* g, double* ke, double* enstrophy);
+
+/* Same quantities written to device memory out_dev[0..1]; asynchronous. */
+SBLI_API int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev);
+
+/* Number of stages completed since creation or the last set_state/init. */
+SBLI_API int sbli_stage_count(const sbli_grid* g, long long* stages);
+
+/* Message describing the last failure on this host thread ("" if none). */
+SBLI_API const char* sbli_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBLI_H */

@@ -1,0 +1,528 @@
+// api.cu -- the C ABI of include/sbli.h: grid handles over caller-owned
+// device memory, stage sequencing of the low-storage scheme (§2.2, Fig. 1),
+// CUDA-graph step loops and the binary64 diagnostics.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "sbli_internal.cuh"
+
+using namespace sbli;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SBLI_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define SBLI_TRY(expr, what)                       \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+  size_t reg64;      // bytes of one binary64 state register (5P doubles)
+  size_t reg32;      // bytes of one binary32 stage register (5P floats)
+  int n64, n32;      // registers of each kind
+  size_t partials;   // bytes of the reduction scratch
+  size_t storeall;   // bytes of the store-all scratch
+  size_t total;
+};
+
+bool valid_sizes(int n0, int n1, int n2) {
+  if (n0 < 5 || n1 < 5 || n2 < 5) return false;
+  // in-plane offsets are 32-bit in the kernels; grid index fits 2^31 planes
+  if ((long long)n0 * n1 >= (1LL << 31)) return false;
+  if (n0 > (1 << 24) || n1 > (1 << 24) || n2 > (1 << 24)) return false;
+  return true;
+}
+
+FusedConfig default_config(const Geom& g, int precision);
+
+Layout layout_for(int n0, int n1, int n2, int precision, int variant) {
+  Geom g{n0, n1, n2, (long long)n0 * n1 * n2};
+  Layout L{};
+  L.reg64 = align_up((size_t)g.P * 5 * sizeof(double));
+  L.reg32 = align_up((size_t)g.P * 5 * sizeof(float));
+  L.n64 = precision == SBLI_FP64 ? 3 : 2;
+  L.n32 = precision == SBLI_FP64 ? 0 : 2;
+  // partial sums: the fused kernel's CTAs for any configuration the grid may
+  // use (the smallest zc gives the most CTAs), or the KE kernel's blocks
+  const long long tiles = (long long)((n0 + 31) / 32) * ((n1 + 3) / 4);
+  const long long max_ctas = tiles * ((n2 + 3) / 4);
+  const long long np = std::max<long long>(max_ctas, ke_num_partials(g));
+  L.partials = align_up((size_t)(2 * np + 2) * sizeof(double));
+  L.storeall = variant == SBLI_STORE_ALL
+                   ? align_up(storeall_scratch_doubles(g, precision == SBLI_FP64 ? 8 : 4) * sizeof(double))
+                   : 0;
+  L.total = L.reg64 * L.n64 + L.reg32 * L.n32 + L.partials + L.storeall;
+  return L;
+}
+
+}  // namespace
+
+struct sbli_grid {
+  int n[3];
+  int precision, variant;
+  sbli_params params;
+  Geom geom;
+  cudaStream_t stream;      // caller's stream (work and graph launches)
+  cudaStream_t cap_stream;  // private stream used only to record graphs
+  Layout layout;
+  double* reg64[3];
+  float* reg32[2];
+  double* partials;  // reduction scratch; last two doubles hold a (ke, ens) result
+  double* ke_out;
+  void* storeall;
+  int state;       // index of the binary64 register holding Q^n (deviation form)
+  int next_stage;  // 0, 1, 2
+  long long stages_done;
+  FusedConfig cfg;
+  Coef<double> cd;
+  Coef<float> cf;
+  RefState ref;
+  // graph of GRAPH_STEPS steps per starting register rotation
+  static constexpr int GRAPH_STEPS = 6;
+  cudaGraphExec_t graph[3];
+  double graph_dt[3];
+};
+
+namespace {
+
+FusedConfig default_config(const Geom& g, int precision) {
+  // Tile 32 x 8; choose planes per CTA to balance waves over 152 SMs: cost
+  // model = waves * (zc + 1.5) (the 4 prologue planes cost about 1.5 full
+  // planes of work), minimised over zc.
+  FusedConfig cfg;
+  cfg.ty = 8;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = precision == SBLI_FP64 ? 1 : 2;
+  const long long slots = (long long)sms * per_sm;
+  const long long tiles = (long long)((g.n0 + 31) / 32) * ((g.n1 + cfg.ty - 1) / cfg.ty);
+  double best = 1e300;
+  int best_zc = g.n2;
+  for (int zc = 4; zc <= g.n2; ++zc) {
+    const long long gz = (g.n2 + zc - 1) / zc;
+    if ((gz - 1) * zc >= g.n2) continue;  // same gz as a smaller zc
+    const long long ctas = tiles * gz;
+    const long long waves = (ctas + slots - 1) / slots;
+    const double cost = (double)waves * (zc + 1.5);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_zc = zc;
+    }
+  }
+  cfg.zc = std::max(4, std::min(best_zc, g.n2));
+  return cfg;
+}
+
+// Pointers of stage k for the current rotation.
+struct StagePtrs {
+  const void* q_in;
+  bool in64;
+  const double* acc_in;
+  double* acc_out;
+  void* q_out;
+  bool out64;
+};
+
+StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
+  StagePtrs p{};
+  if (g->precision == SBLI_FP64) {
+    double* S = g->reg64[state];
+    double* A = g->reg64[(state + 1) % 3];
+    double* B = g->reg64[(state + 2) % 3];
+    p.in64 = p.out64 = true;
+    if (k == 0) {
+      p.q_in = S; p.acc_in = S; p.acc_out = A; p.q_out = B;
+    } else if (k == 1) {
+      p.q_in = B; p.acc_in = A; p.acc_out = A; p.q_out = S;
+    } else {
+      p.q_in = S; p.acc_in = A; p.acc_out = A; p.q_out = nullptr;
+    }
+  } else {
+    double* S = g->reg64[state];
+    double* A = g->reg64[1 - state];
+    p.out64 = false;
+    if (k == 0) {
+      p.q_in = S; p.in64 = true; p.acc_in = S; p.acc_out = A; p.q_out = g->reg32[0];
+    } else if (k == 1) {
+      p.q_in = g->reg32[0]; p.in64 = false; p.acc_in = A; p.acc_out = A; p.q_out = g->reg32[1];
+    } else {
+      p.q_in = g->reg32[1]; p.in64 = false; p.acc_in = A; p.acc_out = A; p.q_out = nullptr;
+    }
+  }
+  return p;
+}
+
+int next_state(const sbli_grid* g, int state) { return g->precision == SBLI_FP64 ? (state + 1) % 3 : 1 - state; }
+
+// Enqueue stage k on stream s for the given rotation; ke_partials != nullptr
+// (stage 0 only) also accumulates the diagnostics of the stage input.
+cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_partials, cudaStream_t s) {
+  const StagePtrs p = stage_ptrs(g, k, state);
+  const double a_dt = RK_A[k] * dt, b_dt = RK_B[k] * dt;
+  if (g->variant == SBLI_FUSED) {
+    StageArgs a{};
+    a.g = g->geom;
+    a.zc = g->cfg.zc;
+    a.q_in = p.q_in;
+    a.acc_in = p.acc_in;
+    a.acc_out = p.acc_out;
+    a.q_out = p.q_out;
+    a.a_dt = a_dt;
+    a.b_dt = b_dt;
+    a.ke_partials = ke_partials;
+    if (g->precision == SBLI_FP64) return launch_fused_fp64(a, g->cd, g->cfg, false, s);
+    return launch_fused_fp32(a, g->cf, g->cfg, p.in64, false, s);
+  }
+  // store-all: residual into scratch, then the update kernel
+  cudaError_t e;
+  if (g->precision == SBLI_FP64) {
+    double* scr = static_cast<double*>(g->storeall);
+    e = launch_storeall_rhs_fp64(g->geom, g->cd, static_cast<const double*>(p.q_in), scr, nullptr, s);
+    if (e != cudaSuccess) return e;
+    const double* r = scr + storeall_r_offset(g->geom);
+    return launch_rk_update(g->geom, r, true, p.acc_in, p.acc_out, p.q_out, true, a_dt, b_dt, s);
+  }
+  float* scr = static_cast<float*>(g->storeall);
+  e = launch_storeall_rhs_fp32(g->geom, g->cf, p.q_in, p.in64, scr, nullptr, s);
+  if (e != cudaSuccess) return e;
+  const float* r = scr + storeall_r_offset(g->geom);
+  return launch_rk_update(g->geom, r, false, p.acc_in, p.acc_out, p.q_out, false, a_dt, b_dt, s);
+}
+
+int check_grid(const sbli_grid* g) {
+  if (!g) return fail(SBLI_EINVAL, "null grid handle");
+  return SBLI_OK;
+}
+
+void drop_graphs(sbli_grid* g) {
+  for (int r = 0; r < 3; ++r) {
+    if (g->graph[r]) cudaGraphExecDestroy(g->graph[r]);
+    g->graph[r] = nullptr;
+    g->graph_dt[r] = 0.0;
+  }
+}
+
+// Record GRAPH_STEPS steps starting from rotation `state` into an executable graph.
+int build_graph(sbli_grid* g, int state, double dt) {
+  if (g->graph[state] && g->graph_dt[state] == dt) return SBLI_OK;
+  if (g->graph[state]) {
+    cudaGraphExecDestroy(g->graph[state]);
+    g->graph[state] = nullptr;
+  }
+  SBLI_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  int st = state;
+  cudaError_t err = cudaSuccess;
+  for (int s = 0; s < sbli_grid::GRAPH_STEPS && err == cudaSuccess; ++s) {
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = enqueue_stage(g, k, st, dt, nullptr, g->cap_stream);
+    st = next_state(g, st);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+  if (err != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(err, "kernel launch during graph capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return cuda_fail(e3, "cudaGraphInstantiate");
+  g->graph[state] = exec;
+  g->graph_dt[state] = dt;
+  return SBLI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbli_abi_version(void) { return SBLI_ABI_VERSION; }
+
+const char* sbli_last_error(void) { return g_last_error.c_str(); }
+
+int sbli_workspace_bytes(int n0, int n1, int n2, int precision, int variant, size_t* bytes) {
+  if (!bytes) return fail(SBLI_EINVAL, "bytes is null");
+  if (!valid_sizes(n0, n1, n2)) return fail(SBLI_EINVAL, "grid %d x %d x %d: each edge must be >= 5 and n0*n1 < 2^31", n0, n1, n2);
+  if (precision != SBLI_FP64 && precision != SBLI_FP32) return fail(SBLI_EINVAL, "unknown precision %d", precision);
+  if (variant != SBLI_FUSED && variant != SBLI_STORE_ALL) return fail(SBLI_EINVAL, "unknown variant %d", variant);
+  *bytes = layout_for(n0, n1, n2, precision, variant).total;
+  return SBLI_OK;
+}
+
+int sbli_create_grid(sbli_grid** out, int n0, int n1, int n2, int precision, int variant, const sbli_params* params,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return fail(SBLI_EINVAL, "out is null");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = sbli_workspace_bytes(n0, n1, n2, precision, variant, &need);
+  if (rc != SBLI_OK) return rc;
+  if (!params) return fail(SBLI_EINVAL, "params is null");
+  const sbli_params& p = *params;
+  if (!(p.Re > 0) || !(p.Mach > 0) || !(p.Pr > 0) || !(p.gamma > 1) || !(p.L > 0) || isnan(p.Re) ||
+      !isfinite(p.Mach) || !isfinite(p.Pr) || !isfinite(p.gamma) || !isfinite(p.L))
+    return fail(SBLI_EINVAL, "invalid physical parameters (Re=%g M=%g Pr=%g gamma=%g L=%g)", p.Re, p.Mach, p.Pr,
+                p.gamma, p.L);
+  if (!workspace) return fail(SBLI_EINVAL, "workspace is null");
+  if (((uintptr_t)workspace) % ALIGN) return fail(SBLI_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < need)
+    return fail(SBLI_ENOMEM, "workspace has %zu bytes, grid needs %zu", workspace_bytes, need);
+  cudaPointerAttributes attr;
+  cudaError_t pe = cudaPointerGetAttributes(&attr, workspace);
+  if (pe != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(SBLI_EINVAL, "workspace is not device memory");
+  }
+
+  sbli_grid* g = new sbli_grid();
+  memset(g->graph, 0, sizeof g->graph);
+  g->n[0] = n0; g->n[1] = n1; g->n[2] = n2;
+  g->precision = precision;
+  g->variant = variant;
+  g->params = p;
+  g->geom = Geom{n0, n1, n2, (long long)n0 * n1 * n2};
+  g->stream = static_cast<cudaStream_t>(stream);
+  g->layout = layout_for(n0, n1, n2, precision, variant);
+  char* w = static_cast<char*>(workspace);
+  for (int r = 0; r < g->layout.n64; ++r, w += g->layout.reg64) g->reg64[r] = reinterpret_cast<double*>(w);
+  for (int r = 0; r < g->layout.n32; ++r, w += g->layout.reg32) g->reg32[r] = reinterpret_cast<float*>(w);
+  g->partials = reinterpret_cast<double*>(w);
+  g->ke_out = g->partials + (g->layout.partials / sizeof(double) - 2);
+  w += g->layout.partials;
+  g->storeall = g->layout.storeall ? static_cast<void*>(w) : nullptr;
+  g->state = 0;
+  g->next_stage = 0;
+  g->stages_done = 0;
+  g->cfg = default_config(g->geom, precision);
+  g->cd = make_coef<double>(g->n, p);
+  g->cf = make_coef<float>(g->n, p);
+  g->ref = make_ref(p);
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  }
+  *out = g;
+  return SBLI_OK;
+}
+
+int sbli_destroy_grid(sbli_grid* g) {
+  if (!g) return SBLI_OK;
+  cudaStreamSynchronize(g->stream);
+  drop_graphs(g);
+  cudaStreamDestroy(g->cap_stream);
+  delete g;
+  return SBLI_OK;
+}
+
+int sbli_init_tgv(sbli_grid* g, double amplitude) {
+  if (int rc = check_grid(g)) return rc;
+  if (!isfinite(amplitude)) return fail(SBLI_EINVAL, "amplitude must be finite");
+  g->state = 0;
+  g->next_stage = 0;
+  g->stages_done = 0;
+  SBLI_TRY(launch_init_tgv(g->geom, g->params, amplitude, g->reg64[0], g->stream), "init_tgv launch");
+  return SBLI_OK;
+}
+
+int sbli_set_state(sbli_grid* g, const double* q, int q_is_host) {
+  if (int rc = check_grid(g)) return rc;
+  if (!q) return fail(SBLI_EINVAL, "q is null");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "set_state between stages of a step (next stage %d)", g->next_stage);
+  const size_t bytes = 5 * (size_t)g->geom.P * sizeof(double);
+  // stage through a free register, then convert to deviation form
+  const int dst = g->state;
+  double* tmp = g->reg64[(dst + 1) % g->layout.n64];
+  if (q_is_host) {
+    SBLI_TRY(cudaMemcpyAsync(tmp, q, bytes, cudaMemcpyHostToDevice, g->stream), "cudaMemcpyAsync H2D");
+  } else {
+    SBLI_TRY(cudaMemcpyAsync(tmp, q, bytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync D2D");
+  }
+  SBLI_TRY(launch_to_offset(g->geom, g->ref, tmp, g->reg64[dst], g->stream), "to_offset launch");
+  if (q_is_host) SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
+  g->stages_done = 0;
+  return SBLI_OK;
+}
+
+int sbli_get_state(sbli_grid* g, double* q, int q_is_host) {
+  if (int rc = check_grid(g)) return rc;
+  if (!q) return fail(SBLI_EINVAL, "q is null");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "get_state between stages of a step (next stage %d)", g->next_stage);
+  const size_t bytes = 5 * (size_t)g->geom.P * sizeof(double);
+  double* tmp = g->reg64[(g->state + 1) % g->layout.n64];
+  SBLI_TRY(launch_from_offset(g->geom, g->ref, g->reg64[g->state], tmp, g->stream), "from_offset launch");
+  if (q_is_host) {
+    SBLI_TRY(cudaMemcpyAsync(q, tmp, bytes, cudaMemcpyDeviceToHost, g->stream), "cudaMemcpyAsync D2H");
+    SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
+  } else {
+    SBLI_TRY(cudaMemcpyAsync(q, tmp, bytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync D2D");
+  }
+  return SBLI_OK;
+}
+
+int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host) {
+  if (int rc = check_grid(g)) return rc;
+  if (g->next_stage == 0) return fail(SBLI_EINVAL, "get_stage outside a step (no stage in progress)");
+  const size_t n = 5 * (size_t)g->geom.P;
+  const StagePtrs p = stage_ptrs(g, g->next_stage, g->state);
+  // convert through the binary64 register this stage does not read
+  auto copy_out = [&](const void* src, bool src64, double* dst) -> int {
+    double* tmp = nullptr;
+    if (g->precision == SBLI_FP64) {
+      // the register not used by this stage holds nothing live
+      for (int r = 0; r < 3; ++r)
+        if (g->reg64[r] != p.q_in && g->reg64[r] != p.acc_in) tmp = g->reg64[r];
+    } else {
+      tmp = g->reg64[g->state];  // Q^n is not needed after stage 0
+    }
+    if (!tmp) return fail(SBLI_EINVAL, "no free register");
+    if (src64) {
+      SBLI_TRY(launch_from_offset(g->geom, g->ref, static_cast<const double*>(src), tmp, g->stream), "from_offset");
+    } else {
+      SBLI_TRY(launch_widen(5 * g->geom.P, static_cast<const float*>(src), tmp, g->stream), "widen");
+      SBLI_TRY(launch_from_offset(g->geom, g->ref, tmp, tmp, g->stream), "from_offset");
+    }
+    SBLI_TRY(cudaMemcpyAsync(dst, tmp, n * sizeof(double), q_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                             g->stream),
+             "cudaMemcpyAsync");
+    if (q_is_host) SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
+    return SBLI_OK;
+  };
+  if (q_stage)
+    if (int rc = copy_out(p.q_in, p.in64, q_stage)) return rc;
+  if (q_acc)
+    if (int rc = copy_out(p.acc_in, true, q_acc)) return rc;
+  return SBLI_OK;
+}
+
+int sbli_rhs(sbli_grid* g, double* r_dev) {
+  if (int rc = check_grid(g)) return rc;
+  if (!r_dev) return fail(SBLI_EINVAL, "r_dev is null");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "rhs between stages of a step");
+  const double* q = g->reg64[g->state];
+  if (g->variant == SBLI_FUSED) {
+    StageArgs a{};
+    a.g = g->geom;
+    a.zc = g->cfg.zc;
+    a.q_in = q;
+    a.r_out = r_dev;
+    cudaError_t e = g->precision == SBLI_FP64 ? launch_fused_fp64(a, g->cd, g->cfg, true, g->stream)
+                                              : launch_fused_fp32(a, g->cf, g->cfg, true, true, g->stream);
+    SBLI_TRY(e, "fused rhs launch");
+    return SBLI_OK;
+  }
+  if (g->precision == SBLI_FP64) {
+    SBLI_TRY(launch_storeall_rhs_fp64(g->geom, g->cd, q, static_cast<double*>(g->storeall), r_dev, g->stream),
+             "store-all rhs");
+    return SBLI_OK;
+  }
+  // binary32 residual, widened to binary64
+  float* scr = static_cast<float*>(g->storeall);
+  SBLI_TRY(launch_storeall_rhs_fp32(g->geom, g->cf, q, true, scr, nullptr, g->stream), "store-all rhs");
+  SBLI_TRY(launch_widen(5 * g->geom.P, scr + storeall_r_offset(g->geom), r_dev, g->stream), "widen residual");
+  return SBLI_OK;
+}
+
+int sbli_rk_stage(sbli_grid* g, int stage, double dt) {
+  if (int rc = check_grid(g)) return rc;
+  if (stage < 0 || stage > 2) return fail(SBLI_EINVAL, "stage %d not in 0..2", stage);
+  if (stage != g->next_stage) return fail(SBLI_EINVAL, "stage %d called, stage %d expected", stage, g->next_stage);
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBLI_EINVAL, "dt must be finite and > 0");
+  SBLI_TRY(enqueue_stage(g, stage, g->state, dt, nullptr, g->stream), "stage launch");
+  g->next_stage = (stage + 1) % 3;
+  if (stage == 2) g->state = next_state(g, g->state);
+  g->stages_done++;
+  return SBLI_OK;
+}
+
+int sbli_step_n(sbli_grid* g, int nsteps, double dt) {
+  if (int rc = check_grid(g)) return rc;
+  if (nsteps < 0) return fail(SBLI_EINVAL, "nsteps < 0");
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBLI_EINVAL, "dt must be finite and > 0");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "step_n must start at a step boundary");
+  int left = nsteps;
+  while (left >= sbli_grid::GRAPH_STEPS) {
+    if (int rc = build_graph(g, g->state, dt)) return rc;
+    SBLI_TRY(cudaGraphLaunch(g->graph[g->state], g->stream), "cudaGraphLaunch");
+    // GRAPH_STEPS is a multiple of the rotation period (3 and 2)
+    left -= sbli_grid::GRAPH_STEPS;
+    g->stages_done += 3 * sbli_grid::GRAPH_STEPS;
+  }
+  for (; left > 0; --left) {
+    for (int k = 0; k < 3; ++k) SBLI_TRY(enqueue_stage(g, k, g->state, dt, nullptr, g->stream), "stage launch");
+    g->state = next_state(g, g->state);
+    g->stages_done += 3;
+  }
+  return SBLI_OK;
+}
+
+int sbli_step_n_history(sbli_grid* g, int nsteps, double dt, double* ke_hist_dev) {
+  if (int rc = check_grid(g)) return rc;
+  if (nsteps < 0) return fail(SBLI_EINVAL, "nsteps < 0");
+  if (!ke_hist_dev && nsteps > 0) return fail(SBLI_EINVAL, "ke_hist_dev is null");
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBLI_EINVAL, "dt must be finite and > 0");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "step_n_history must start at a step boundary");
+  if (g->variant != SBLI_FUSED) return fail(SBLI_EUNSUPPORTED, "history needs the fused variant");
+  const int nctas = fused_num_ctas(g->geom, g->cfg);
+  for (int s = 0; s < nsteps; ++s) {
+    SBLI_TRY(enqueue_stage(g, 0, g->state, dt, g->partials, g->stream), "stage launch");
+    SBLI_TRY(launch_finalize_ke(g->partials, nctas, 1.0 / (double)g->geom.P, ke_hist_dev + 2 * s, g->stream),
+             "finalize launch");
+    for (int k = 1; k < 3; ++k) SBLI_TRY(enqueue_stage(g, k, g->state, dt, nullptr, g->stream), "stage launch");
+    g->state = next_state(g, g->state);
+    g->stages_done += 3;
+  }
+  return SBLI_OK;
+}
+
+int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev) {
+  if (int rc = check_grid(g)) return rc;
+  if (!out_dev) return fail(SBLI_EINVAL, "out_dev is null");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "kinetic_energy between stages of a step");
+  SBLI_TRY(launch_ke(g->geom, g->cd, g->ref, g->reg64[g->state], g->partials, out_dev, g->stream), "ke launch");
+  return SBLI_OK;
+}
+
+int sbli_kinetic_energy(sbli_grid* g, double* ke, double* enstrophy) {
+  if (int rc = check_grid(g)) return rc;
+  if (!ke || !enstrophy) return fail(SBLI_EINVAL, "null output pointer");
+  if (int rc = sbli_kinetic_energy_async(g, g->ke_out)) return rc;
+  double h[2];
+  SBLI_TRY(cudaMemcpyAsync(h, g->ke_out, sizeof h, cudaMemcpyDeviceToHost, g->stream), "cudaMemcpyAsync D2H");
+  SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
+  *ke = h[0];
+  *enstrophy = h[1];
+  return SBLI_OK;
+}
+
+int sbli_stage_count(const sbli_grid* g, long long* stages) {
+  if (!g || !stages) return fail(SBLI_EINVAL, "null argument");
+  *stages = g->stages_done;
+  return SBLI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,41 @@
+// fused_fp32.cu -- binary32 instantiations of the fused stage kernel.  The
+// stage input is binary64 at stage 0 (the state between steps) and binary32
+// at stages 1-2; the accumulator is always binary64.
+#include "fused_stage.cuh"
+
+namespace sbli {
+
+template <int TY>
+static cudaError_t dispatch32(const StageArgs& a, const Coef<float>& c, bool in_fp64, bool rhs_only,
+                              cudaStream_t s) {
+  if (rhs_only) {
+    if (in_fp64) return launch_fused_t<float, double, float, TY, true, false>(a, c, s);
+    return launch_fused_t<float, float, float, TY, true, false>(a, c, s);
+  }
+  if (in_fp64) {
+    if (a.ke_partials) return launch_fused_t<float, double, float, TY, false, true>(a, c, s);
+    return launch_fused_t<float, double, float, TY, false, false>(a, c, s);
+  }
+  return launch_fused_t<float, float, float, TY, false, false>(a, c, s);
+}
+
+cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
+                              bool rhs_only, cudaStream_t s) {
+  switch (cfg.ty) {
+    case 4: return dispatch32<4>(a, c, in_fp64, rhs_only, s);
+    case 8: return dispatch32<8>(a, c, in_fp64, rhs_only, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int fused_num_ctas(const Geom& g, const FusedConfig& cfg) {
+  const long long gx = (g.n0 + TX - 1) / TX, gy = (g.n1 + cfg.ty - 1) / cfg.ty, gz = (g.n2 + cfg.zc - 1) / cfg.zc;
+  return (int)(gx * gy * gz);
+}
+
+size_t fused_smem_bytes(int elem_bytes, int ty) {
+  if (elem_bytes == 8) return ty == 4 ? sizeof(FusedSmem<double, 4>) : sizeof(FusedSmem<double, 8>);
+  return ty == 4 ? sizeof(FusedSmem<float, 4>) : sizeof(FusedSmem<float, 8>);
+}
+
+}  // namespace sbli

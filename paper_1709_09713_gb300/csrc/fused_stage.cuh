@@ -1,0 +1,399 @@
+// fused_stage.cuh -- fused residual + low-storage RK stage kernel (sm_103a).
+//
+// One kernel evaluates R(Q) of Eqs. 1-3 (arXiv:1709.09713, §2) with every
+// derivative of Eqs. 6-7 computed on the fly (no derivative arrays: the
+// "store none" class of §2.5, ordered by velocity component as in SN2) and
+// writes the Runge-Kutta stage of §2.2 / Fig. 1 in the same pass.
+//
+// Work decomposition (2.5D streaming):
+//   * a CTA owns a 32 x TY tile of (x0, x1) columns and marches along x2
+//     over zc planes; one thread per column, a warp is one x0 row, so every
+//     global access is a coalesced row segment;
+//   * a ring of 5 shared-memory slots holds the primitives of planes
+//     z-2..z+2 on the tile plus a 2-point halo in x0 and x1 (corners
+//     included).  A plane's primitives are computed once, when it enters the
+//     ring, from the conserved variables loaded from HBM (periodic wrap in
+//     the index arithmetic replaces the boundary pass of Fig. 1);
+//   * x0/x1 derivatives read the centre slot, x2 derivatives read the ring;
+//   * the mixed second derivatives of the stress divergence use, for each i,
+//       sum_{j != i} d2 u_j/dx_i dx_j = D1_i( s_i ),  s_i = sum_{j != i} D1_j u_j,
+//     (linearity of D1_i; the D1_a o D1_b reading of the mixed term), so
+//     only the three diagonal gradients D1_j u_j are needed around a point:
+//     D1_x u0 and D1_y u1 are kept per plane, D1_z u2 is formed on the
+//     centre plane's tile and halo.
+//
+// Variables are stored as deviations from the reference state
+// (rho' = rho - 1, rho u_i, (rho E)' = rho E - p_ref/(gamma-1)), which keeps
+// binary32 storage free of the low-Mach cancellation in rho E; the residual
+// is the same algebraic expression (the constant parts of rho E and p enter
+// only through the reference enthalpy term -H0 div u).
+#pragma once
+
+#include "sbli_internal.cuh"
+
+namespace sbli {
+
+constexpr int TX = 32;  // tile width along x0 (one warp)
+constexpr int HALO = 2;
+constexpr int SX = TX + 2 * HALO;
+constexpr int NSLOT = 5;
+
+// primitive values kept per point in a ring slot
+enum { V_RHO, V_M0, V_M1, V_M2, V_E, V_U0, V_U1, V_U2, V_P, V_T, NV };
+
+template <typename T, int TY>
+struct FusedSmem {
+  static constexpr int SY = TY + 2 * HALO;
+  T ring[NSLOT][NV][SY][SX];  // rho', m_i, E', u_i, p', T' per haloed point
+  T dring[NSLOT][2][TY][TX];  // D1_x u0 and D1_y u1 per plane (tile only)
+  T s0buf[TY][SX];            // s_0 = D1_y u1 + D1_z u2, centre plane, x0-haloed rows
+  T s1buf[SY][TX];            // s_1 = D1_x u0 + D1_z u2, centre plane, x1-haloed columns
+  double red[2][32];          // block reduction of (ke, enstrophy)
+};
+
+template <typename T>
+__device__ __forceinline__ T rcp_rn(T x);
+template <>
+__device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
+template <>
+__device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+
+// Accumulated terms of the residual at one point.
+template <typename T>
+struct Terms {
+  T g[3][3];   // g[i][j] = D1_j u_i
+  T rrho;      // sum_j D_j m_j + u_j D_j rho'                    (Eq. 1 without rho div u)
+  T rm[3];     // sum_{j != i} D_j(m_i u_j) + u_j D_j m_i         (Eq. 2 without m_i div u)
+  T rmx[3];    // -D_i(m_i u_i / 2 + p')                          (Eq. 2 diagonal product + pressure)
+  T rE1;       // sum_j D_j((E'/2 + p') u_j)                      (Eq. 3 E'u and p'u fluxes)
+  T rE2;       // sum_j u_j D_j E'
+  T lap[3];    // sum_j D2_j u_i
+  T lapT;      // sum_j D2_j T'
+  T G[3];      // sum_j d2 u_j / dx_i dx_j (Eq. 7 on j = i, D1 o D1 otherwise)
+};
+
+// All derivatives along axis A at one point.  nb(v, k) returns primitive v
+// at the neighbour k = 0..3 (offsets -2, -1, +1, +2 along A); uc, Tc are the
+// centre values; s[k] the mixed-term helper s_A at the neighbours.
+template <int A, typename T, typename NB>
+__device__ __forceinline__ void axis_terms(const NB& nb, const T (&s)[4], const Coef<T>& c, const T (&uc)[3], T Tc,
+                                           Terms<T>& t) {
+  const T c1 = c.c1[A], c2 = c.c2[A], e0 = c.e0[A], e1 = c.e1[A], e2 = c.e2[A];
+  auto d1 = [&](T fm2, T fm1, T fp1, T fp2) { return c1 * (fp1 - fm1) - c2 * (fp2 - fm2); };
+  auto d2 = [&](T fm2, T fm1, T f0, T fp1, T fp2) { return e0 * f0 + e1 * (fp1 + fm1) + e2 * (fp2 + fm2); };
+
+  T rho[4], m[3][4], E[4], u[3][4], p[4], Tt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    rho[k] = nb(V_RHO, k);
+    m[0][k] = nb(V_M0, k);
+    m[1][k] = nb(V_M1, k);
+    m[2][k] = nb(V_M2, k);
+    E[k] = nb(V_E, k);
+    u[0][k] = nb(V_U0, k);
+    u[1][k] = nb(V_U1, k);
+    u[2][k] = nb(V_U2, k);
+    p[k] = nb(V_P, k);
+    Tt[k] = nb(V_T, k);
+  }
+  const T ua = uc[A];
+  const T Drho = d1(rho[0], rho[1], rho[2], rho[3]);
+  const T DE = d1(E[0], E[1], E[2], E[3]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T Dm = d1(m[i][0], m[i][1], m[i][2], m[i][3]);
+    if (i == A) {
+      t.rrho += Dm + ua * Drho;
+      t.rm[i] += ua * Dm;
+      T P[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) P[k] = T(0.5) * m[A][k] * u[A][k] + p[k];
+      t.rmx[i] -= d1(P[0], P[1], P[2], P[3]);
+    } else {
+      T P[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) P[k] = m[i][k] * u[A][k];
+      t.rm[i] += d1(P[0], P[1], P[2], P[3]) + ua * Dm;
+      t.g[i][A] = d1(u[i][0], u[i][1], u[i][2], u[i][3]);
+    }
+  }
+  {
+    T PE[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) PE[k] = (T(0.5) * E[k] + p[k]) * u[A][k];
+    t.rE1 += d1(PE[0], PE[1], PE[2], PE[3]);
+  }
+  t.rE2 += ua * DE;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T l = d2(u[i][0], u[i][1], uc[i], u[i][2], u[i][3]);
+    t.lap[i] += l;
+    if (i == A) t.G[A] = l + d1(s[0], s[1], s[2], s[3]);
+  }
+  t.lapT += d2(Tt[0], Tt[1], Tc, Tt[2], Tt[3]);
+}
+
+// TIN: type of the stage input in HBM; TOUT: type of the stage output.
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
+__global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
+    fused_stage_kernel(const StageArgs a, const Coef<T> c) {
+  using S = FusedSmem<T, TY>;
+  constexpr int SY = S::SY;
+  constexpr int NT = TX * TY;
+  constexpr int PTS = SX * SY;
+  constexpr int LPT = (PTS + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S& sm = *reinterpret_cast<S*>(smem_raw);
+
+  const int n0 = a.g.n0, n1 = a.g.n1, n2 = a.g.n2;
+  const long long P = a.g.P;
+  const long long plane = (long long)n0 * n1;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int zbeg = blockIdx.z * a.zc;
+  const int zend = min(zbeg + a.zc, n2);
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid_xy = (gx < n0) && (gy < n1);
+  const long long own_off = valid_xy ? (gx + (long long)n0 * gy) : 0;
+  const TIN* __restrict__ qin = static_cast<const TIN*>(a.q_in);
+
+  // haloed points this thread loads on every plane (periodic wrap)
+  int ld_off[LPT], ld_s[LPT];
+#pragma unroll
+  for (int l = 0; l < LPT; ++l) {
+    const int idx = tid + l * NT;
+    if (idx < PTS) {
+      const int sy = idx / SX, sx = idx % SX;
+      ld_off[l] = wrapi(x0 - HALO + sx, n0) + n0 * wrapi(y0 - HALO + sy, n1);
+      ld_s[l] = sy * SX + sx;
+    } else {
+      ld_off[l] = -1;
+      ld_s[l] = 0;
+    }
+  }
+
+  double ke_acc = 0.0, ens_acc = 0.0;
+  const int nplanes = zend - zbeg;
+  T d22 = T(0);
+
+  for (int it = 0; it < nplanes + 4; ++it) {
+    // ---------------------------------------------------------------- phase 1
+    // plane e = zbeg - 2 + it enters slot it % 5: load Q', derive primitives
+    // (Eqs. 4-5 in deviation form) on the haloed tile.
+    const int se = it % NSLOT;
+    {
+      const long long zoff = (long long)wrapi(zbeg - HALO + it, n2) * plane;
+      T* ring = &sm.ring[se][0][0][0];
+      constexpr int PL = SY * SX;
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        if (ld_off[l] >= 0) {
+          const long long o = zoff + ld_off[l];
+          const T rho_p = T(qin[o]);
+          const T m0 = T(qin[P + o]);
+          const T m1 = T(qin[2 * P + o]);
+          const T m2 = T(qin[3 * P + o]);
+          const T E_p = T(qin[4 * P + o]);
+          const T rinv = rcp_rn<T>(T(1) + rho_p);
+          const T u0 = m0 * rinv, u1 = m1 * rinv, u2 = m2 * rinv;
+          const T mu = m0 * u0 + m1 * u1 + m2 * u2;
+          const T p_p = c.gm1 * (E_p - T(0.5) * mu);          // Eq. 4: p - p_ref
+          const T T_p = (c.gM2 * p_p - rho_p) * rinv;         // Eq. 5: T - 1
+          const int s = ld_s[l];
+          ring[V_RHO * PL + s] = rho_p;
+          ring[V_M0 * PL + s] = m0;
+          ring[V_M1 * PL + s] = m1;
+          ring[V_M2 * PL + s] = m2;
+          ring[V_E * PL + s] = E_p;
+          ring[V_U0 * PL + s] = u0;
+          ring[V_U1 * PL + s] = u1;
+          ring[V_U2 * PL + s] = u2;
+          ring[V_P * PL + s] = p_p;
+          ring[V_T * PL + s] = T_p;
+        }
+      }
+    }
+    __syncthreads();
+    // --------------------------------------------------------------- phase 2a
+    // in-plane diagonal gradients of the entering plane, kept for s_2 and
+    // for the velocity gradient when the plane is the centre.
+    {
+      const T(*U0)[SX] = sm.ring[se][V_U0];
+      const T(*U1)[SX] = sm.ring[se][V_U1];
+      const int sy = ty + HALO, sx = tx + HALO;
+      sm.dring[se][0][ty][tx] = c.c1[0] * (U0[sy][sx + 1] - U0[sy][sx - 1]) - c.c2[0] * (U0[sy][sx + 2] - U0[sy][sx - 2]);
+      sm.dring[se][1][ty][tx] = c.c1[1] * (U1[sy + 1][sx] - U1[sy - 1][sx]) - c.c2[1] * (U1[sy + 2][sx] - U1[sy - 2][sx]);
+    }
+    if (it < 4) continue;  // ring not yet full; slots written so far are not read again before the next sync
+
+    const int zc = zbeg + it - 4;  // centre plane
+    // slot of plane zc + o, o = -2..2
+    int sl[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) sl[o] = (it + 1 + o) % NSLOT;
+    const int scen = sl[2];
+
+    // --------------------------------------------------------------- phase 2b
+    // s_0 and s_1 on the centre plane's tile and halo.
+    {
+      const int sy = ty + HALO, sx = tx + HALO;
+      auto u2z = [&](int yy, int xx) {
+        return c.c1[2] * (sm.ring[sl[3]][V_U2][yy][xx] - sm.ring[sl[1]][V_U2][yy][xx]) -
+               c.c2[2] * (sm.ring[sl[4]][V_U2][yy][xx] - sm.ring[sl[0]][V_U2][yy][xx]);
+      };
+      d22 = u2z(sy, sx);
+      sm.s0buf[ty][sx] = sm.dring[scen][1][ty][tx] + d22;
+      sm.s1buf[sy][tx] = sm.dring[scen][0][ty][tx] + d22;
+      const T(*U0)[SX] = sm.ring[scen][V_U0];
+      const T(*U1)[SX] = sm.ring[scen][V_U1];
+      for (int h = tid; h < 4 * (TX + TY); h += NT) {
+        if (h < 4 * TY) {
+          const int r = h >> 2, k = h & 3;
+          const int hx = (k < 2) ? k : TX + k;  // 0, 1, TX+2, TX+3
+          const int hy = r + HALO;
+          const T d11 = c.c1[1] * (U1[hy + 1][hx] - U1[hy - 1][hx]) - c.c2[1] * (U1[hy + 2][hx] - U1[hy - 2][hx]);
+          sm.s0buf[r][hx] = d11 + u2z(hy, hx);
+        } else {
+          const int h2 = h - 4 * TY;
+          const int col = h2 % TX, k = h2 / TX;
+          const int hy = (k < 2) ? k : TY + k;
+          const int hx = col + HALO;
+          const T d00 = c.c1[0] * (U0[hy][hx + 1] - U0[hy][hx - 1]) - c.c2[0] * (U0[hy][hx + 2] - U0[hy][hx - 2]);
+          sm.s1buf[hy][col] = d00 + u2z(hy, hx);
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- phase 3
+    {
+      const int sy = ty + HALO, sx = tx + HALO;
+      const T(*C)[SY][SX] = sm.ring[scen];
+      const T rho_p = C[V_RHO][sy][sx];
+      const T mc[3] = {C[V_M0][sy][sx], C[V_M1][sy][sx], C[V_M2][sy][sx]};
+      const T Ec = C[V_E][sy][sx];
+      const T uc[3] = {C[V_U0][sy][sx], C[V_U1][sy][sx], C[V_U2][sy][sx]};
+      const T Tc = C[V_T][sy][sx];
+
+      Terms<T> t;
+      t.rrho = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        t.rm[i] = T(0);
+        t.rmx[i] = T(0);
+        t.lap[i] = T(0);
+      }
+      t.rE1 = t.rE2 = t.lapT = T(0);
+      t.g[0][0] = sm.dring[scen][0][ty][tx];
+      t.g[1][1] = sm.dring[scen][1][ty][tx];
+      t.g[2][2] = d22;
+
+      // x0: velocity component 0 group first (SN2 ordering), then x1, x2
+      {
+        const T s[4] = {sm.s0buf[ty][sx - 2], sm.s0buf[ty][sx - 1], sm.s0buf[ty][sx + 1], sm.s0buf[ty][sx + 2]};
+        const int off[4] = {-2, -1, 1, 2};
+        auto nb = [&](int v, int k) { return C[v][sy][sx + off[k]]; };
+        axis_terms<0>(nb, s, c, uc, Tc, t);
+      }
+      {
+        const T s[4] = {sm.s1buf[sy - 2][tx], sm.s1buf[sy - 1][tx], sm.s1buf[sy + 1][tx], sm.s1buf[sy + 2][tx]};
+        const int off[4] = {-2, -1, 1, 2};
+        auto nb = [&](int v, int k) { return C[v][sy + off[k]][sx]; };
+        axis_terms<1>(nb, s, c, uc, Tc, t);
+      }
+      {
+        const int zs[4] = {sl[0], sl[1], sl[3], sl[4]};
+        T s[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s[k] = sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx];
+        auto nb = [&](int v, int k) { return sm.ring[zs[k]][v][sy][sx]; };
+        axis_terms<2>(nb, s, c, uc, Tc, t);
+      }
+
+      // assemble Eqs. 1-3
+      const T div = t.g[0][0] + t.g[1][1] + t.g[2][2];
+      const T rho = T(1) + rho_p;
+      T R[5];
+      R[0] = T(-0.5) * (t.rrho + rho * div);
+      T uvisc = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T visc = t.lap[i] + t.G[i] * T(1.0 / 3.0);  // Laplacian + G - (2/3) G
+        uvisc += uc[i] * visc;
+        R[1 + i] = T(-0.5) * (t.rm[i] + mc[i] * div) + t.rmx[i] + c.inv_re * visc;
+      }
+      // viscous dissipation du_i/dx_j (du_i/dx_j + du_j/dx_i - 2/3 div delta_ij)
+      const T a01 = t.g[0][1] + t.g[1][0], a02 = t.g[0][2] + t.g[2][0], a12 = t.g[1][2] + t.g[2][1];
+      const T diss = T(2) * (t.g[0][0] * t.g[0][0] + t.g[1][1] * t.g[1][1] + t.g[2][2] * t.g[2][2]) + a01 * a01 +
+                     a02 * a02 + a12 * a12 - T(2.0 / 3.0) * div * div;
+      R[4] = -t.rE1 - T(0.5) * (t.rE2 + Ec * div) - c.H0 * div + c.inv_re * (uvisc + diss) + c.kappa * t.lapT;
+
+      if (valid_xy) {
+        const long long o = (long long)zc * plane + own_off;
+        if (RHS_ONLY) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) a.r_out[f * P + o] = double(R[f]);
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const double accv = a.acc_in ? a.acc_in[f * P + o] : double(qin[f * P + o]);
+            const double r = double(R[f]);
+            a.acc_out[f * P + o] = fma(a.b_dt, r, accv);
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[f * P + o] = TOUT(fma(a.a_dt, r, accv));
+          }
+        }
+        if (WITH_KE) {
+          const T w0 = t.g[2][1] - t.g[1][2], w1 = t.g[0][2] - t.g[2][0], w2 = t.g[1][0] - t.g[0][1];
+          ke_acc += double(T(0.5) * (mc[0] * uc[0] + mc[1] * uc[1] + mc[2] * uc[2]));
+          ens_acc += double(T(0.5) * rho * (w0 * w0 + w1 * w1 + w2 * w2));
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (WITH_KE) {
+    // fixed-order block reduction: warp shuffles, then warp 0 over warps
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ke_acc += __shfl_down_sync(0xffffffffu, ke_acc, o);
+      ens_acc += __shfl_down_sync(0xffffffffu, ens_acc, o);
+    }
+    if ((tid & 31) == 0) {
+      sm.red[0][tid >> 5] = ke_acc;
+      sm.red[1][tid >> 5] = ens_acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double k = 0.0, e = 0.0;
+      for (int w = 0; w < NT / 32; ++w) {
+        k += sm.red[0][w];
+        e += sm.red[1][w];
+      }
+      const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      a.ke_partials[2 * b] = k;
+      a.ke_partials[2 * b + 1] = e;
+    }
+  }
+}
+
+template <int TY>
+inline dim3 fused_grid(const Geom& g, int zc) {
+  return dim3((g.n0 + TX - 1) / TX, (g.n1 + TY - 1) / TY, (g.n2 + zc - 1) / zc);
+}
+
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
+cudaError_t launch_fused_t(const StageArgs& a, const Coef<T>& c, cudaStream_t s) {
+  auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE>;
+  const size_t smem = sizeof(FusedSmem<T, TY>);
+  static bool configured = false;  // one attribute call per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k<<<fused_grid<TY>(a.g, a.zc), TX * TY, smem, s>>>(a, c);
+  return cudaGetLastError();
+}
+
+}  // namespace sbli

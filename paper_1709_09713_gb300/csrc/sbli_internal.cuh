@@ -1,0 +1,119 @@
+// sbli_internal.cuh -- shared definitions of the CUDA library (not part of
+// the public ABI).  Kernels and launchers for one grid are declared here and
+// defined in the per-precision translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sbli.h"
+
+namespace sbli {
+
+// Number of fields of the state Q = (rho, rho u0, rho u1, rho u2, rho E).
+constexpr int NF = 5;
+
+// Per-grid constants in the arithmetic type T of the kernel.  All
+// divisions by the grid spacing and by physical constants are folded here
+// once (as the paper's generated code does, §2.6).
+template <typename T>
+struct Coef {
+  // Eq. 6: D1 f = c1 (f[+1] - f[-1]) - c2 (f[+2] - f[-2]),
+  //   c1 = 2/(3h), c2 = 1/(12h)
+  T c1[3], c2[3];
+  // Eq. 7: D2 f = e0 f[0] + e1 (f[+1] + f[-1]) + e2 (f[+2] + f[-2]),
+  //   e0 = -5/(2h^2), e1 = 4/(3h^2), e2 = -1/(12h^2)
+  T e0[3], e1[3], e2[3];
+  T gm1;    // gamma - 1                    (Eq. 4)
+  T gM2;    // gamma M^2                    (Eq. 5)
+  T inv_re; // 1/Re (0 for Re = inf)        (Eqs. 2-3)
+  T kappa;  // 1/((gamma-1) M^2 Pr Re)      (Eq. 3 heat flux)
+  T H0;     // (rho E)_ref + p_ref = 1/((gamma-1) M^2): enthalpy of the reference state
+};
+
+// Reference state the stored variables are measured from:
+//   rho_ref = 1, (rho u)_ref = 0, (rho E)_ref = p_ref/(gamma-1),
+//   p_ref = 1/(gamma M^2)  (so T_ref = 1 by Eq. 5).
+struct RefState {
+  double rho0, E0;
+};
+
+template <typename T>
+Coef<T> make_coef(const int n[3], const sbli_params& p);
+
+RefState make_ref(const sbli_params& p);
+
+// Runge-Kutta coefficients of the two-register three-stage scheme (§2.2):
+// stage a_k and accumulator b_k, third order (a_2 = b_2).
+constexpr double RK_A[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
+constexpr double RK_B[3] = {1.0 / 4.0, 3.0 / 20.0, 3.0 / 5.0};
+
+// Geometry passed to every kernel.
+struct Geom {
+  int n0, n1, n2;
+  long long P;  // n0*n1*n2
+};
+
+// Arguments of one fused stage (or RHS-only) launch.
+struct StageArgs {
+  Geom g;
+  int zc;                  // planes per CTA along x2
+  const void* q_in;        // stage input (stencil reads)
+  const double* acc_in;    // accumulator in (binary64), nullptr: use q_in (stage 0)
+  double* acc_out;         // accumulator out (binary64), may alias acc_in
+  void* q_out;             // stage output, nullptr on the last stage
+  double* r_out;           // RHS-only mode: R (binary64)
+  double a_dt, b_dt;       // a_k dt, b_k dt
+  double* ke_partials;     // per-CTA (ke, enstrophy) partial sums, or nullptr
+};
+
+// Launch configuration chosen for one grid (the autotuner's output).
+struct FusedConfig {
+  int ty;  // in-plane tile height (tile is 32 x ty)
+  int zc;  // planes per CTA
+};
+
+// Host launchers (defined in fused_fp64.cu / fused_fp32.cu).
+// in_fp64: stage input is binary64 (FP64 path, or FP32 path at stage 0).
+// out_fp64: stage output is binary64.
+cudaError_t launch_fused_fp64(const StageArgs& a, const Coef<double>& c, const FusedConfig& cfg, bool rhs_only,
+                              cudaStream_t s);
+cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
+                              bool rhs_only, cudaStream_t s);
+int fused_num_ctas(const Geom& g, const FusedConfig& cfg);
+size_t fused_smem_bytes(int elem_bytes, int ty);
+
+// Diagnostics and state conversion (diag.cu).
+cudaError_t launch_init_tgv(const Geom& g, const sbli_params& p, double amplitude, double* q, cudaStream_t s);
+cudaError_t launch_to_offset(const Geom& g, const RefState& r, const double* q_plain, double* q_off, cudaStream_t s);
+cudaError_t launch_from_offset(const Geom& g, const RefState& r, const double* q_off, double* q_plain,
+                               cudaStream_t s);
+// dst[i] = (double)src[i], i < n
+cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_t s);
+// KE/enstrophy of a binary64 offset state: per-CTA partials into scratch,
+// then a fixed-order final sum into out[0..1].
+int ke_num_partials(const Geom& g);
+cudaError_t launch_ke(const Geom& g, const Coef<double>& c, const RefState& r, const double* q_off,
+                      double* partials, double* out, cudaStream_t s);
+// Fixed-order sum of n (ke, ens) pairs, scaled by 1/P.
+cudaError_t launch_finalize_ke(const double* partials, int n, double inv_p, double* out, cudaStream_t s);
+
+// Store-all (BL) variant (storeall.cu).
+size_t storeall_scratch_doubles(const Geom& g, int elem_bytes);
+// element offset of the residual R inside the store-all scratch
+long long storeall_r_offset(const Geom& g);
+cudaError_t launch_storeall_rhs_fp64(const Geom& g, const Coef<double>& c, const double* q_off, double* scratch,
+                                     double* r_out, cudaStream_t s);
+cudaError_t launch_storeall_rhs_fp32(const Geom& g, const Coef<float>& c, const void* q_off, bool in_fp64,
+                                     float* scratch, float* r_out, cudaStream_t s);
+cudaError_t launch_rk_update(const Geom& g, const void* r, bool r_fp64, const double* acc_in, double* acc_out,
+                             void* q_out, bool out_fp64, double a_dt, double b_dt, cudaStream_t s);
+
+// Wrap i into [0, n) for |i| < 2^30.
+__host__ __device__ inline int wrapi(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+}  // namespace sbli

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of the C ABI in include/sbli.h.
+
+Every ``sbli_*`` function here has the same name and arguments as the C
+entry point and only marshals arguments; all arithmetic runs in
+``lib/libsbli.so``.  PyTorch supplies device memory (the workspace) and the
+CUDA stream.  ``Grid`` is a small convenience owner of one handle and its
+workspace tensor.  There is no CPU fallback: if the library is missing,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsbli.so")
+
+SBLI_OK, SBLI_EINVAL, SBLI_ENOMEM, SBLI_ECUDA, SBLI_ETIMEOUT, SBLI_EUNSUPPORTED = range(6)
+SBLI_FP64, SBLI_FP32 = 0, 1
+SBLI_FUSED, SBLI_STORE_ALL = 0, 1
+
+# Every entry point the header declares, with its ctypes signature.
+_c_int, _c_double, _c_size_t, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Re", _c_double), ("Mach", _c_double), ("Pr", _c_double), ("gamma", _c_double), ("L", _c_double)]
+
+
+SIGNATURES = {
+    "sbli_abi_version": (_c_int, []),
+    "sbli_workspace_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_c_size_t)]),
+    "sbli_create_grid": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_int, _c_int,
+                                  ctypes.POINTER(Params), _vp, _c_size_t, _vp]),
+    "sbli_destroy_grid": (_c_int, [_vp]),
+    "sbli_init_tgv": (_c_int, [_vp, _c_double]),
+    "sbli_set_state": (_c_int, [_vp, _vp, _c_int]),
+    "sbli_get_state": (_c_int, [_vp, _vp, _c_int]),
+    "sbli_get_stage": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "sbli_rhs": (_c_int, [_vp, _vp]),
+    "sbli_rk_stage": (_c_int, [_vp, _c_int, _c_double]),
+    "sbli_step_n": (_c_int, [_vp, _c_int, _c_double]),
+    "sbli_step_n_history": (_c_int, [_vp, _c_int, _c_double, _vp]),
+    "sbli_kinetic_energy": (_c_int, [_vp, _DP, _DP]),
+    "sbli_kinetic_energy_async": (_c_int, [_vp, _vp]),
+    "sbli_stage_count": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sbli_last_error": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SbliError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sbli error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsbli.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != SBLI_OK:
+        raise SbliError(rc, lib().sbli_last_error().decode())
+
+
+def params(Re=1600.0, Mach=0.1, Pr=0.71, gamma=1.4, L=1.0) -> Params:
+    return Params(float(Re), float(Mach), float(Pr), float(gamma), float(L))
+
+
+# ---- same-name wrappers of the C entry points (status codes become exceptions)
+
+def sbli_abi_version() -> int:
+    return lib().sbli_abi_version()
+
+
+def sbli_workspace_bytes(n0: int, n1: int, n2: int, precision: int, variant: int) -> int:
+    out = _c_size_t()
+    _check(lib().sbli_workspace_bytes(n0, n1, n2, precision, variant, ctypes.byref(out)))
+    return out.value
+
+
+def sbli_create_grid(n0, n1, n2, precision, variant, prm: Params, workspace_ptr: int, workspace_bytes: int,
+                     stream: int) -> int:
+    h = _vp()
+    _check(lib().sbli_create_grid(ctypes.byref(h), n0, n1, n2, precision, variant, ctypes.byref(prm),
+                                  _vp(workspace_ptr), workspace_bytes, _vp(stream)))
+    return h.value
+
+
+def sbli_destroy_grid(h: int) -> None:
+    _check(lib().sbli_destroy_grid(_vp(h)))
+
+
+def sbli_init_tgv(h: int, amplitude: float = 1.0) -> None:
+    _check(lib().sbli_init_tgv(_vp(h), float(amplitude)))
+
+
+def sbli_set_state(h: int, q_ptr: int, q_is_host: bool) -> None:
+    _check(lib().sbli_set_state(_vp(h), _vp(q_ptr), int(bool(q_is_host))))
+
+
+def sbli_get_state(h: int, q_ptr: int, q_is_host: bool) -> None:
+    _check(lib().sbli_get_state(_vp(h), _vp(q_ptr), int(bool(q_is_host))))
+
+
+def sbli_get_stage(h: int, q_stage_ptr: int, q_acc_ptr: int, q_is_host: bool) -> None:
+    _check(lib().sbli_get_stage(_vp(h), _vp(q_stage_ptr), _vp(q_acc_ptr), int(bool(q_is_host))))
+
+
+def sbli_rhs(h: int, r_ptr: int) -> None:
+    _check(lib().sbli_rhs(_vp(h), _vp(r_ptr)))
+
+
+def sbli_rk_stage(h: int, stage: int, dt: float) -> None:
+    _check(lib().sbli_rk_stage(_vp(h), int(stage), float(dt)))
+
+
+def sbli_step_n(h: int, nsteps: int, dt: float) -> None:
+    _check(lib().sbli_step_n(_vp(h), int(nsteps), float(dt)))
+
+
+def sbli_step_n_history(h: int, nsteps: int, dt: float, hist_ptr: int) -> None:
+    _check(lib().sbli_step_n_history(_vp(h), int(nsteps), float(dt), _vp(hist_ptr)))
+
+
+def sbli_kinetic_energy(h: int) -> tuple[float, float]:
+    ke, ens = _c_double(), _c_double()
+    _check(lib().sbli_kinetic_energy(_vp(h), ctypes.byref(ke), ctypes.byref(ens)))
+    return ke.value, ens.value
+
+
+def sbli_kinetic_energy_async(h: int, out_ptr: int) -> None:
+    _check(lib().sbli_kinetic_energy_async(_vp(h), _vp(out_ptr)))
+
+
+def sbli_stage_count(h: int) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().sbli_stage_count(_vp(h), ctypes.byref(v)))
+    return v.value
+
+
+def sbli_last_error() -> str:
+    return lib().sbli_last_error().decode()
+
+
+# ---- convenience owner (torch tensors for memory and stream)
+
+class Grid:
+    """One grid: a workspace tensor on the current CUDA device plus a handle.
+
+    ``n`` is an int (cube) or (n0, n1, n2).  State tensors exchanged with the
+    library have shape (5, n2, n1, n0), float64, x0 fastest.
+    """
+
+    def __init__(self, n, precision=SBLI_FP64, variant=SBLI_FUSED, Re=1600.0, Mach=0.1, Pr=0.71, gamma=1.4, L=1.0,
+                 stream=None, device=None):
+        import torch
+
+        self.n = (n, n, n) if isinstance(n, int) else tuple(int(v) for v in n)
+        self.precision, self.variant = precision, variant
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.prm = params(Re, Mach, Pr, gamma, L)
+        self.bytes = sbli_workspace_bytes(*self.n, precision, variant)
+        self.workspace = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.handle = sbli_create_grid(*self.n, precision, variant, self.prm, aligned, self.bytes,
+                                       self.stream.cuda_stream)
+
+    @property
+    def shape(self):
+        return (5, self.n[2], self.n[1], self.n[0])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sbli_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_tgv(self, amplitude=1.0):
+        sbli_init_tgv(self.handle, amplitude)
+
+    def set_state(self, q):
+        import torch
+
+        assert q.dtype == torch.float64 and q.is_contiguous() and tuple(q.shape) == self.shape
+        sbli_set_state(self.handle, q.data_ptr(), not q.is_cuda)
+
+    def get_state(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        assert out.dtype == torch.float64 and out.is_contiguous() and tuple(out.shape) == self.shape
+        sbli_get_state(self.handle, out.data_ptr(), not out.is_cuda)
+        return out
+
+    def rhs(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        sbli_rhs(self.handle, out.data_ptr())
+        return out
+
+    def get_stage(self):
+        """(Q_k, Q_acc) between stages, as plain binary64 device tensors."""
+        import torch
+
+        qs = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        qa = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        sbli_get_stage(self.handle, qs.data_ptr(), qa.data_ptr(), False)
+        return qs, qa
+
+    def rk_stage(self, stage, dt):
+        sbli_rk_stage(self.handle, stage, dt)
+
+    def step_n(self, nsteps, dt):
+        sbli_step_n(self.handle, nsteps, dt)
+
+    def step_n_history(self, nsteps, dt):
+        import torch
+
+        hist = torch.empty((max(nsteps, 1), 2), dtype=torch.float64, device=self.device)
+        sbli_step_n_history(self.handle, nsteps, dt, hist.data_ptr())
+        return hist[:nsteps]
+
+    def kinetic_energy(self):
+        return sbli_kinetic_energy(self.handle)
+
+    def stage_count(self):
+        return sbli_stage_count(self.handle)

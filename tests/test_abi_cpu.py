@@ -1,0 +1,97 @@
+"""CPU-side checks of the C ABI: the library loads without a GPU, exports
+every entry point include/sbli.h declares, and rejects invalid arguments
+that need no device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sbli():
+    from paper_1709_09713_gb300 import build
+
+    build.build()
+    from paper_1709_09713_gb300 import sbli as S
+
+    S.lib()
+    return S
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sbli.h")).read()
+    return sorted(set(re.findall(r"SBLI_API\s+(?:const\s+)?\w+\*?\s+\*?(sbli_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["sbli_create_grid", "sbli_init_tgv", "sbli_rhs", "sbli_rk_stage", "sbli_step_n",
+                     "sbli_kinetic_energy", "sbli_destroy_grid", "sbli_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(sbli):
+    lib = ctypes.CDLL(sbli.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    # the binding wraps every declared function with the same name
+    for name in declared_functions():
+        assert name in sbli.SIGNATURES, name
+        assert callable(getattr(sbli, name))
+
+
+def test_exports_only_the_abi(sbli):
+    import subprocess
+
+    out = subprocess.run(["nm", "-D", "--defined-only", sbli.LIB_PATH], capture_output=True, text=True).stdout
+    syms = [line.split()[-1] for line in out.splitlines() if line.strip()]
+    assert syms and all(s.startswith("sbli_") for s in syms), [s for s in syms if not s.startswith("sbli_")]
+
+
+def test_version(sbli):
+    assert sbli.sbli_abi_version() == 1
+
+
+@pytest.mark.parametrize("n", [(4, 8, 8), (8, 4, 8), (8, 8, 4), (0, 8, 8), (-3, 8, 8)])
+def test_rejects_grids_below_stencil_width(sbli, n):
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(*n, sbli.SBLI_FP64, sbli.SBLI_FUSED)
+    assert e.value.code == sbli.SBLI_EINVAL
+    assert "5" in sbli.sbli_last_error()
+
+
+def test_rejects_unknown_modes(sbli):
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(8, 8, 8, 7, sbli.SBLI_FUSED)
+    assert e.value.code == sbli.SBLI_EINVAL
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(8, 8, 8, sbli.SBLI_FP64, 9)
+    assert e.value.code == sbli.SBLI_EINVAL
+
+
+def test_workspace_sizes(sbli):
+    P = 32**3
+    f64 = sbli.sbli_workspace_bytes(32, 32, 32, sbli.SBLI_FP64, sbli.SBLI_FUSED)
+    f32 = sbli.sbli_workspace_bytes(32, 32, 32, sbli.SBLI_FP32, sbli.SBLI_FUSED)
+    bl = sbli.sbli_workspace_bytes(32, 32, 32, sbli.SBLI_FP64, sbli.SBLI_STORE_ALL)
+    assert f64 >= 3 * 5 * P * 8 and f64 < 3 * 5 * P * 8 + (1 << 20)
+    assert f32 >= 2 * 5 * P * 8 + 2 * 5 * P * 4
+    assert bl >= f64 + 82 * P * 8
+
+
+def test_null_arguments_are_errors(sbli):
+    lib = sbli.lib()
+    assert lib.sbli_workspace_bytes(8, 8, 8, 0, 0, None) == sbli.SBLI_EINVAL
+    assert lib.sbli_create_grid(None, 8, 8, 8, 0, 0, None, None, 0, None) == sbli.SBLI_EINVAL
+    assert lib.sbli_rk_stage(None, 0, 1e-3) == sbli.SBLI_EINVAL
+    assert lib.sbli_destroy_grid(None) == sbli.SBLI_OK
+    h = ctypes.c_void_p()
+    prm = sbli.params()
+    # null workspace is rejected before any device call
+    assert lib.sbli_create_grid(ctypes.byref(h), 8, 8, 8, 0, 0, ctypes.byref(prm), None, 0, None) == sbli.SBLI_EINVAL
+    bad = sbli.params(Re=-1.0)
+    assert lib.sbli_create_grid(ctypes.byref(h), 8, 8, 8, 0, 0, ctypes.byref(bad), None, 0, None) == sbli.SBLI_EINVAL
+    assert "param" in sbli.sbli_last_error()

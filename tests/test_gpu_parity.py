@@ -1,0 +1,229 @@
+"""GPU path (through the C ABI) against the CPU oracle on identical inputs.
+
+Tolerances (relative max-norm per field; the three momentum fields share the
+denominator max_i |rho u_i| because rho u2 starts at zero):
+  * binary64 state after the stated steps: 1e-12 (the stated FP64 bar);
+  * binary64 residual on random states: 1e-12;
+  * binary32 stage storage and arithmetic with binary64 accumulation: state
+    1e-5, kinetic-energy history 1e-6 (the stated FP32 bars); residual 1e-4
+    (binary32 arithmetic: eps = 6e-8 times the ~1e3 amplification of the
+    derivative stencils and cancellations in the energy equation).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1709_09713_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GAMMA, MACH = 1.4, 0.1
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_09713_gb300 import build
+
+    build.build()
+    from paper_1709_09713_gb300 import sbli
+
+    sbli.lib()
+    return sbli
+
+
+def rel_fields(a, b):
+    """Per-field relative max-norm error, momentum with a shared denominator."""
+    out = []
+    mom = max(np.max(np.abs(b[1:4])), 1e-300)
+    for f in range(5):
+        den = mom if 1 <= f <= 3 else max(np.max(np.abs(b[f])), 1e-300)
+        out.append(float(np.max(np.abs(a[f] - b[f])) / den))
+    return out
+
+
+def random_state(n, seed):
+    e0 = 1.0 / (GAMMA * (GAMMA - 1.0) * MACH**2) + 0.5
+    return workloads.smooth_state(n, seed, offsets=(1.0, 0.0, 0.0, 0.0, e0), amplitudes=(0.05, 0.5, 0.5, 0.5, 0.5))
+
+
+def to_dev(q):
+    return torch.from_numpy(np.ascontiguousarray(q)).cuda()
+
+
+GRIDS = [(32, 32, 32), (40, 24, 20), (37, 11, 9), (5, 5, 5), (5, 6, 7), (64, 16, 8)]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("n", GRIDS)
+def test_rhs_fp64_matches_oracle(S, orc, n, variant):
+    q = random_state(n, seed=sum(n))
+    g = S.Grid(n, S.SBLI_FP64, variant)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    want = orc.rhs(orc.params(n), q)
+    errs = rel_fields(r, want)
+    assert max(errs) <= 1e-12, errs
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("n", [(32, 32, 32), (40, 24, 20), (5, 6, 7)])
+def test_rhs_fp32_matches_oracle(S, orc, n, variant):
+    q = random_state(n, seed=3 + sum(n))
+    g = S.Grid(n, S.SBLI_FP32, variant)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    want = orc.rhs(orc.params(n), q)
+    errs = rel_fields(r, want)
+    assert max(errs) <= 1e-4, errs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_init_tgv_matches_oracle(S, orc, precision):
+    n = (32, 24, 16)
+    for A in (1.0, 0.93):
+        g = S.Grid(n, precision, S.SBLI_FUSED)
+        g.init_tgv(A)
+        got = g.get_state().cpu().numpy()
+        want = orc.init_tgv(orc.params(n), A)
+        assert max(rel_fields(got, want)) <= 1e-14
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tgv_32_fp64_ten_steps(S, orc, variant):
+    """The 32^3 Taylor-Green case (Re 1600, M 0.1, dt 1e-3, 10 steps):
+    fused and store-all binary64 paths against the oracle, <= 1e-12."""
+    n, dt, steps = 32, 1e-3, 10
+    g = S.Grid(n, S.SBLI_FP64, variant)
+    g.init_tgv(1.0)
+    g.step_n(steps, dt)
+    got = g.get_state().cpu().numpy()
+    p = orc.params(n)
+    want = orc.step(p, orc.init_tgv(p), dt, steps)
+    errs = rel_fields(got, want)
+    assert max(errs) <= 1e-12, errs
+    assert g.stage_count() == 3 * steps
+
+
+def test_stages_one_by_one_match_oracle(S, orc):
+    """Each stage's outputs (stage field and accumulator) against the oracle's
+    two-register stage, on a random ragged grid, binary64."""
+    n, dt = (24, 20, 12), 2e-3
+    q0 = random_state(n, seed=77)
+    g = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
+    g.set_state(to_dev(q0))
+    p = orc.params(n)
+    q_in, acc = q0.copy(), q0.copy()
+    for k in range(3):
+        g.rk_stage(k, dt)
+        q_out, acc = orc.stage(p, k, dt, q_in, acc)
+        if k < 2:
+            qs, qa = (t.cpu().numpy() for t in g.get_stage())
+            assert max(rel_fields(qs, q_out)) <= 1e-13
+            assert max(rel_fields(qa, acc)) <= 1e-13
+        q_in = q_out
+    got = g.get_state().cpu().numpy()
+    assert max(rel_fields(got, acc)) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_steps_equal_stage_calls(S, precision):
+    """sbli_step_n (captured graph, 6-step chunks + remainder) is bitwise the
+    same as calling the stages one by one."""
+    n, dt, steps = (32, 16, 16), 1e-3, 8
+    a = S.Grid(n, precision, S.SBLI_FUSED)
+    b = S.Grid(n, precision, S.SBLI_FUSED)
+    a.init_tgv()
+    b.init_tgv()
+    a.step_n(steps, dt)
+    for _ in range(steps):
+        for k in range(3):
+            b.rk_stage(k, dt)
+    assert torch.equal(a.get_state(), b.get_state())
+
+
+def test_fused_and_storeall_agree(S):
+    n, dt = (32, 24, 16), 1e-3
+    a = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
+    b = S.Grid(n, S.SBLI_FP64, S.SBLI_STORE_ALL)
+    q = to_dev(random_state(n, 5))
+    a.set_state(q)
+    b.set_state(q)
+    a.step_n(4, dt)
+    b.step_n(4, dt)
+    assert max(rel_fields(a.get_state().cpu().numpy(), b.get_state().cpu().numpy())) <= 1e-13
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tgv_fp32_against_fp64_oracle(S, orc, variant):
+    """Binary32 storage/arithmetic with binary64 accumulation, 32^3 TGV,
+    10 steps: fields within 1e-5, KE within 1e-6 of the binary64 oracle."""
+    n, dt, steps = 32, 1e-3, 10
+    g = S.Grid(n, S.SBLI_FP32, variant)
+    g.init_tgv(1.0)
+    g.step_n(steps, dt)
+    got = g.get_state().cpu().numpy()
+    p = orc.params(n)
+    want = orc.step(p, orc.init_tgv(p), dt, steps)
+    errs = rel_fields(got, want)
+    assert max(errs) <= 1e-5, errs
+    ke, ens = g.kinetic_energy()
+    ke_o, ens_o = orc.ke_enstrophy(p, want)
+    assert abs(ke - ke_o) / ke_o <= 1e-6
+
+
+@pytest.mark.parametrize("n", [(32, 32, 32), (20, 12, 28), (5, 5, 5)])
+def test_kinetic_energy_matches_oracle(S, orc, n):
+    q = random_state(n, seed=19)
+    g = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
+    g.set_state(to_dev(q))
+    ke, ens = g.kinetic_energy()
+    ke_o, ens_o = orc.ke_enstrophy(orc.params(n), q)
+    assert ke == pytest.approx(ke_o, rel=1e-13)
+    assert ens == pytest.approx(ens_o, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-6)])
+def test_history_matches_oracle(S, orc, precision, tol):
+    """KE/enstrophy of Q^n before each step, fused into stage 0."""
+    n, dt, steps = 24, 1e-3, 5
+    g = S.Grid(n, precision, S.SBLI_FUSED)
+    g.init_tgv()
+    hist = g.step_n_history(steps, dt).cpu().numpy()
+    p = orc.params(n)
+    q = orc.init_tgv(p)
+    for s in range(steps):
+        ke_o, ens_o = orc.ke_enstrophy(p, q)
+        assert abs(hist[s, 0] - ke_o) / ke_o <= tol
+        assert abs(hist[s, 1] - ens_o) / ens_o <= tol * 10
+        q = orc.step(p, q, dt, 1)
+
+
+def test_error_paths_fault_nothing(S):
+    g = S.Grid(16, S.SBLI_FP64, S.SBLI_FUSED)
+    g.init_tgv()
+    with pytest.raises(S.SbliError) as e:
+        g.rk_stage(1, 1e-3)
+    assert e.value.code == S.SBLI_EINVAL
+    with pytest.raises(S.SbliError):
+        g.rk_stage(0, -1.0)
+    g.rk_stage(0, 1e-3)
+    with pytest.raises(S.SbliError):
+        g.get_state()
+    with pytest.raises(S.SbliError):
+        g.step_n(1, 1e-3)
+    g.rk_stage(1, 1e-3)
+    g.rk_stage(2, 1e-3)
+    g.get_state()
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.SbliError) as e:
+        S.sbli_create_grid(16, 16, 16, 0, 0, S.params(), (small.data_ptr() + 255) // 256 * 256, 512, 0)
+    assert e.value.code == S.SBLI_ENOMEM
+    host = torch.empty(1 << 20, dtype=torch.uint8)
+    with pytest.raises(S.SbliError) as e:
+        S.sbli_create_grid(8, 8, 8, 0, 0, S.params(), (host.data_ptr() + 255) // 256 * 256, 1 << 19, 0)
+    assert e.value.code in (S.SBLI_EINVAL, S.SBLI_ENOMEM)
+    torch.cuda.synchronize()
