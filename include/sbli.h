@@ -142,6 +142,28 @@ SBLI_API int sbli_kinetic_energy(sbli_grid* g, double* ke, double* enstrophy);
 /* Same quantities written to device memory out_dev[0..1]; asynchronous. */
 SBLI_API int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev);
 
+/* Kinetic energy and enstrophy, as sbli_kinetic_energy computes them, of a
+ * state the caller owns, without any device allocation by the caller or the
+ * library.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory (an application that reserves the whole
+ * device up front, code handed only a state pointer, loops that must not
+ * allocate once running) and therefore cannot provide a grid workspace.
+ *   q_dev   device array of 5*n0*n1*n2 binary64 plain conserved variables,
+ *           layout as sbli_get_state writes it (read only);
+ *   L       domain edge / (2 pi) (h_i = 2 pi L / n_i);
+ *   out_dev device array of 2 binary64: (ke, enstrophy) volume averages;
+ *   stream  cudaStream_t the kernels run on (NULL = legacy default stream).
+ * The partial sums live in one static device array of the library, 8192
+ * pairs (128 KiB per GPU, held until the process exits); grids of more than
+ * 8192 * 16384 = 134,217,728 points (512^3) are rejected with SBLI_EINVAL.
+ * The first call on a device looks up that array's device address; make that
+ * first call before any stream capture on the device.  Every call overwrites
+ * the array (each partial sum is written before it is read, so nothing needs
+ * clearing); calls that overlap on the GPU, on any streams, race on it and
+ * must be ordered by the caller.  Asynchronous. */
+SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, int n2, double L, double* out_dev,
+                                         void* stream);
+
 /* Number of stages completed since creation or the last set_state/init. */
 SBLI_API int sbli_stage_count(const sbli_grid* g, long long* stages);
 

@@ -82,6 +82,11 @@ Layout layout_for(int n0, int n1, int n2, int precision, int variant) {
 
 }  // namespace
 
+int sbli::set_last_error(int code, const char* msg) {
+  g_last_error = msg;
+  return code;
+}
+
 struct sbli_grid {
   int n[3];
   int precision, variant;

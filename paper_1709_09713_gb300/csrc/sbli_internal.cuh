@@ -110,6 +110,9 @@ cudaError_t launch_storeall_rhs_fp32(const Geom& g, const Coef<float>& c, const 
 cudaError_t launch_rk_update(const Geom& g, const void* r, bool r_fp64, const double* acc_in, double* acc_out,
                              void* q_out, bool out_fp64, double a_dt, double b_dt, cudaStream_t s);
 
+// Record msg as this host thread's sbli_last_error() and return code.
+int set_last_error(int code, const char* msg);
+
 // Wrap i into [0, n) for |i| < 2^30.
 __host__ __device__ inline int wrapi(int i, int n) {
   int r = i % n;

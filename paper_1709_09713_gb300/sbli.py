@@ -45,6 +45,7 @@ SIGNATURES = {
     "sbli_step_n_history": (_c_int, [_vp, _c_int, _c_double, _vp]),
     "sbli_kinetic_energy": (_c_int, [_vp, _DP, _DP]),
     "sbli_kinetic_energy_async": (_c_int, [_vp, _vp]),
+    "sbli_kinetic_energy_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _vp]),
     "sbli_stage_count": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "sbli_last_error": (ctypes.c_char_p, []),
 }
@@ -148,6 +149,12 @@ def sbli_kinetic_energy(h: int) -> tuple[float, float]:
 
 def sbli_kinetic_energy_async(h: int, out_ptr: int) -> None:
     _check(lib().sbli_kinetic_energy_async(_vp(h), _vp(out_ptr)))
+
+
+def sbli_kinetic_energy_noalloc(q_ptr: int, n0: int, n1: int, n2: int, L: float, out_ptr: int,
+                                stream: int = 0) -> None:
+    """Allocation-free KE/enstrophy of a plain device state (no grid, no workspace)."""
+    _check(lib().sbli_kinetic_energy_noalloc(_vp(q_ptr), n0, n1, n2, float(L), _vp(out_ptr), _vp(stream)))
 
 
 def sbli_stage_count(h: int) -> int:
