@@ -1,26 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the fused Navier-Stokes RHS + RK3 stage on GB300.
 
-Workload (default): Taylor-Green vortex 256^3, binary64, Re 1600, M 0.1,
-dt 1e-3 (§4 of arXiv:1709.09713 at the paper's grid size).  One bench step is
-one time step = 3 fused stages over the whole grid; the metric is
-point-stage updates per second (grid points x stages / s).
+Main workload: Taylor-Green vortex 256^3, binary64, Re 1600, M 0.1,
+dt 1e-3 (the paper's grid, §4 of arXiv:1709.09713), fused on-the-fly kernel.
+One bench step is one time step = 3 fused stages over the whole grid; the
+metric is point-stage updates per second.
 
-Legs printed in the one JSON line:
-  value      device-resident throughput over exactly --steps steps (CUDA
-             events on the grid's stream, barrier + synchronize on both sides,
-             max over ranks);
-  e2e        the same metric through the public C ABI with host buffers:
-             every e2e step copies the initial state from pinned host memory,
-             runs --solve-steps time steps and copies the final state back;
-  roofline   the dominant kernel against its binding roofline;
-  cpu_baseline  the CPU oracle (as it stands) on a bounded sample.
+The JSON line carries:
+  value        device-resident throughput over exactly --steps steps (CUDA
+               events on the grid's stream; barrier + synchronize on both
+               sides; max over ranks);
+  e2e          the same metric through the public C ABI with host buffers:
+               every e2e step copies the initial state from pinned host
+               memory, runs --solve-steps time steps, copies the state back;
+  roofline     the fused stage kernel against its binding roofline (the FP64
+               pipe for binary64; HBM for the binary32 leg);
+  legs         the binary32-storage path at 512^3 (HBM roofline) and the
+               store-all comparison variant at 256^3;
+  energy       NVML total-energy delta per point-stage over the timed region;
+  cpu_baseline the CPU oracle (unchanged) on a bounded sample.
 ``--impl reference`` times only the CPU oracle (the reference arm).
 Multi-GPU (torchrun): independent replicas, one grid per rank (weak scaling).
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -35,21 +40,26 @@ if ROOT not in sys.path:
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# binary64 peak derived from GB300's nominal 1.25 TFLOP/s: 152 SMs x 2 DFMA
+# (4 flop) per clock per SM x SM clock (2.07 GHz max) = 1.259 TFLOP/s
+FP64_FLOP_PER_CLK_PER_SM = 4.0
 
-# Algorithmic HBM bytes per point-stage of the fused kernel (minimum traffic,
-# averaged over the three stages of a step):
-#   binary64: 50 values per point-step / 3 stages * 8 B = 133.3 B
+# Algorithmic HBM bytes per point-stage of the fused kernel, averaged over
+# the three stages of a step (minimum traffic of the two-register scheme):
+#   binary64: 50 values per point-step / 3 * 8 B = 133.3 B
 #   binary32 stage fields + binary64 accumulator: 320 B / 3 = 106.7 B
-ALG_BYTES = {0: 400.0 / 3.0, 1: 320.0 / 3.0}
-# binary64 FLOPs per point-stage executed by the fused kernel (DADD + DMUL +
-# 2 DFMA counted by ncu on the 256^3 stage; see profiles/).
-FUSED_FP64_FLOPS_PER_PT = None
+ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}
+# binary64 flop per point-stage the fused kernel executes (2 DFMA + DADD +
+# DMUL), counted by ncu on the 256^3 stage-1 launch (profiles/).
+FUSED_FP64_FLOP_PER_PT = 578.0
+# DRAM bytes per launch from the same ncu captures (None once stale)
+NCU_TRAFFIC = {("fp64", 256): 2.693e9, ("fp32", 256): 1.977e9}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
@@ -58,16 +68,18 @@ def parse():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--solve-steps", type=int, default=10, help="time steps per e2e solve")
     ap.add_argument("--e2e-reps", type=int, default=2)
+    ap.add_argument("--no-legs", action="store_true", help="skip the FP32 512^3 and store-all legs")
+    ap.add_argument("--leg-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
-    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=3)
     return ap.parse_args()
 
 
-# ----------------------------------------------------------------- clocks
+# ------------------------------------------------------------ clocks, NVML
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -83,8 +95,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -100,7 +111,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
@@ -109,13 +120,37 @@ class ClockSampler:
             try:
                 sm.append(float(parts[1]))
                 smax = float(parts[2])
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             for name, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": statistics.median(power) if power else None}
+
+
+class Nvml:
+    """Total-energy counter of one GPU through libnvidia-ml (ctypes)."""
+
+    def __init__(self, index: int):
+        self.ok = False
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.dev = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.dev)) != 0:
+                return
+            self.ok = self.energy_mj() is not None
+        except OSError:
+            pass
+
+    def energy_mj(self):
+        v = ctypes.c_ulonglong()
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.dev, ctypes.byref(v)) != 0:
+            return None
+        return v.value
 
 
 # --------------------------------------------------------------- helpers
@@ -123,34 +158,79 @@ class ClockSampler:
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def cpu_baseline(n: int, steps: int, dt: float):
-    """Time the CPU oracle (unchanged) on an n^3 TGV for `steps` time steps."""
+    """The CPU oracle, unchanged, on an n^3 TGV for `steps` time steps on all host cores."""
     import oracle
 
     oracle.build()
-    cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    oracle.set_threads(os.cpu_count() or 1)
     p = oracle.params(n)
     q = oracle.init_tgv(p)
     t0 = time.perf_counter()
     oracle.step(p, q, dt, steps)
     el = time.perf_counter() - t0
-    pts = n**3 * 3 * steps
-    return {"value": pts / el, "unit": "pt-stage/s", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"TGV {n}^3 FP64, {steps} time steps ({3 * steps} stages), {el:.2f} s"}
+    return {"value": n**3 * 3 * steps / el, "unit": "pt-stage/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"TGV {n}^3 FP64, {steps} time steps ({3 * steps} stages) in {el:.2f} s"}
+
+
+def time_steps(S, g, stream, steps, dt, ws):
+    """CUDA-event time of exactly `steps` steps on the grid's stream, max over ranks."""
+    import torch
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step_n(steps, dt)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def leg(S, n, precision, variant, steps, warmup, dt, ws):
+    """Throughput of one extra configuration (no e2e, no clocks)."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    prec = S.SBLI_FP64 if precision == "fp64" else S.SBLI_FP32
+    var = S.SBLI_FUSED if variant == "fused" else S.SBLI_STORE_ALL
+    g = S.Grid(n, prec, var, stream=stream)
+    with torch.cuda.stream(stream):
+        g.init_tgv(1.0)
+        g.step_n(warmup, dt)
+    ms = time_steps(S, g, stream, steps, dt, ws)
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    P = n**3
+    stage_ms = ms / (3 * steps)
+    out = {"workload": f"TGV {n}^3 {precision} {variant}", "value": 3.0 * P * steps * ws / (ms / 1e3),
+           "unit": "pt-stage/s", "steps": steps, "stage_ms": stage_ms}
+    if variant == "fused":
+        peaks, kind = measured_peaks()
+        ach = ALG_BYTES[precision] * P / (stage_ms / 1e3) / 1e9
+        out["hbm"] = {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                      "peak_source": kind}
+    return out
 
 
 # ------------------------------------------------------------- our arm
@@ -174,83 +254,69 @@ def run_ours(args):
     S.lib()
     prec = S.SBLI_FP64 if args.precision == "fp64" else S.SBLI_FP32
     var = S.SBLI_FUSED if args.variant == "fused" else S.SBLI_STORE_ALL
-    n, dt = args.n, args.dt
+    n, dt, P = args.n, args.dt, args.n**3
     stream = torch.cuda.Stream()
     g = S.Grid(n, prec, var, stream=stream)
-    P = n**3
 
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
-    # warm-up (also builds the step graphs)
     with torch.cuda.stream(stream):
         g.init_tgv(1.0)
-        for _ in range(args.warmup):
-            g.step_n(1, dt)
+        g.step_n(args.warmup, dt)
     stream.synchronize()
 
-    # device-resident timed region: exactly K steps
+    nvml = Nvml(torch.cuda.current_device())
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    g.step_n(args.steps, dt)
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
+    e_before = nvml.energy_mj() if nvml.ok else None
+    ms = time_steps(S, g, stream, args.steps, dt, ws)
+    e_after = nvml.energy_mj() if nvml.ok else None
     clk = clocks.stop()
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    pt_stages = 3.0 * P * args.steps * ws
-    value = pt_stages / (ms_max / 1e3)
+    value = 3.0 * P * args.steps * ws / (ms / 1e3)
+    stage_ms = ms / (3 * args.steps)  # one fused launch per stage
 
-    # per-launch duration of the dominant kernel: one stage = one launch
-    stage_ms = ms / (3 * args.steps)
-
-    # e2e through the C ABI with host buffers
+    # e2e: initial state from pinned host memory, --solve-steps steps, state back
     q_host = torch.empty(g.shape, dtype=torch.float64).pin_memory()
     r_host = torch.empty(g.shape, dtype=torch.float64).pin_memory()
     g.init_tgv(1.0)
     g.get_state(q_host)
-    e2e_times = []
+    e2e_t = []
     for _ in range(args.e2e_reps):
-        barrier()
+        if ws > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         S.sbli_set_state(g.handle, q_host.data_ptr(), True)
         S.sbli_step_n(g.handle, args.solve_steps, dt)
         S.sbli_get_state(g.handle, r_host.data_ptr(), True)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_t = min(e2e_times)
+        e2e_t.append(time.perf_counter() - t0)
+    t_e2e = min(e2e_t)
     if ws > 1:
-        t = torch.tensor([e2e_t], device="cuda")
+        t = torch.tensor([t_e2e], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = 3.0 * P * args.solve_steps * ws / e2e_t
+        t_e2e = float(t.item())
     state_bytes = 5 * P * 8
+    g.close()
+    del g
+    torch.cuda.empty_cache()
 
     peaks, kind = measured_peaks()
-    if prec == S.SBLI_FP32 and var == S.SBLI_FUSED:
-        alg = ALG_BYTES[1] * P
-        achieved = alg / (stage_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": kind}
+    if prec == S.SBLI_FP64 and var == S.SBLI_FUSED:
+        clock_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_tf = sms * FP64_FLOP_PER_CLK_PER_SM * clock_ghz / 1e3
+        ach = FUSED_FP64_FLOP_PER_PT * P / (stage_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
+                "traffic": NCU_TRAFFIC.get(("fp64", n)),
+                "note": f"binary64 pipe; {FUSED_FP64_FLOP_PER_PT:.0f} flop/pt-stage counted by ncu; peak = {sms} SMs x "
+                        f"4 flop/clk x {clock_ghz:.3f} GHz (median SM clock under load)",
+                "hbm_frac": ALG_BYTES["fp64"] * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
     else:
-        alg = ALG_BYTES[0] * P
-        achieved = alg / (stage_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": kind}
+        pname = "fp64" if prec == S.SBLI_FP64 else "fp32"
+        ach = ALG_BYTES[pname] * P / (stage_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC.get((pname, n)) if var == S.SBLI_FUSED else None,
+                "peak_source": kind}
 
     line = {
         "metric": "pt-stage updates/s",
@@ -259,25 +325,32 @@ def run_ours(args):
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_max / args.steps,
+        "ms_per_step": ms / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64" if prec == S.SBLI_FP64 else "f32 (f64 accumulator)",
-        "data": "synthetic (Taylor-Green vortex initial field, section 4)",
-        "config": {"workload": f"TGV {n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, dt {dt}",
-                   "grid": [n, n, n], "l2": "inputs larger than L2 (state register "
-                   f"{state_bytes / 2**20:.0f} MiB > 129 MB)", "parallelism": f"replicas x{ws}"},
-        "e2e": {"value": e2e_value, "unit": "pt-stage/s", "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes, "solve_steps": args.solve_steps},
+        "data": "synthetic (Taylor-Green vortex initial field of section 4)",
+        "config": {"workload": f"TGV {n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, Pr 0.71, dt {dt}",
+                   "grid": [n, n, n], "l2": f"inputs larger than L2 ({state_bytes / 2**20:.0f} MiB state register)",
+                   "parallelism": f"independent replicas x{ws}"},
+        "e2e": {"value": 3.0 * P * args.solve_steps * ws / t_e2e, "unit": "pt-stage/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "note": f"each e2e step = H2D state + {args.solve_steps} time steps + D2H state"},
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": 3 * args.steps,
         "stage_ms": stage_ms,
     }
+    if e_before is not None and e_after is not None:
+        joules = (e_after - e_before) / 1e3
+        line["energy"] = {"joules": joules, "j_per_pt_stage": joules / (3.0 * P * args.steps),
+                          "source": "nvmlDeviceGetTotalEnergyConsumption delta over the timed region"}
+    if not args.no_legs:
+        line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws),
+                        leg(S, 256, "fp64", "store_all", max(3, args.leg_steps // 4), 1, dt, ws)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_n, args.cpu_sample_steps, dt)
-    g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -285,20 +358,18 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    per_step = []
     import oracle
 
     oracle.build()
-    cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    oracle.set_threads(os.cpu_count() or 1)
     n = args.cpu_sample_n
     p = oracle.params(n)
     q = oracle.init_tgv(p)
-    for _ in range(args.warmup):
-        q = oracle.step(p, q, args.dt, 1)
+    q = oracle.step(p, q, args.dt, args.warmup)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         q = oracle.step(p, q, args.dt, 1)
@@ -307,11 +378,11 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": "pt-stage updates/s", "value": value, "unit": "pt-stage/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Taylor-Green vortex, section 4)",
-        "config": {"workload": f"TGV {args.n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, dt {args.dt}",
-                   "sample": f"CPU oracle on the {n}^3 TGV (bounded sample of the workload)"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Taylor-Green vortex of section 4)",
+        "config": {"workload": f"TGV {args.n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, Pr 0.71, dt {args.dt}",
+                   "grid": [args.n] * 3, "sample": f"each step: one time step of the {n}^3 TGV on the CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "pt-stage/s", "cores": oracle.get_threads(), "kind": "oracle",
-                         "sample": f"TGV {n}^3, {args.steps} time steps"},
+                         "sample": f"TGV {n}^3, {args.steps} time steps after {args.warmup} warm-up steps"},
         "e2e": {"value": value, "unit": "pt-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

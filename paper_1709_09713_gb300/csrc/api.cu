@@ -199,6 +199,7 @@ cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_
     a.q_out = p.q_out;
     a.a_dt = a_dt;
     a.b_dt = b_dt;
+    a.amb_dt = (RK_A[k] - RK_B[k]) * dt;
     a.ke_partials = ke_partials;
     if (g->precision == SBLI_FP64) return launch_fused_fp64(a, g->cd, g->cfg, false, s);
     return launch_fused_fp32(a, g->cf, g->cfg, p.in64, false, s);

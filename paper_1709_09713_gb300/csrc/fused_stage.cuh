@@ -11,9 +11,14 @@
 //     global access is a coalesced row segment;
 //   * a ring of 5 shared-memory slots holds the primitives of planes
 //     z-2..z+2 on the tile plus a 2-point halo in x0 and x1 (corners
-//     included).  A plane's primitives are computed once, when it enters the
-//     ring, from the conserved variables loaded from HBM (periodic wrap in
-//     the index arithmetic replaces the boundary pass of Fig. 1);
+//     included), one 10-value record per point (array of structures, read
+//     with 8- or 16-byte vector loads at bank-conflict-free strides).  A
+//     plane's primitives are computed once, when it enters the ring, from the
+//     conserved variables loaded from HBM (periodic wrap in the index
+//     arithmetic replaces the boundary pass of Fig. 1);
+//   * the loads of the next entering plane are issued as soon as the current
+//     plane is stored, and the centre plane's accumulator values before the
+//     residual is assembled, so HBM latency overlaps the arithmetic;
 //   * x0/x1 derivatives read the centre slot, x2 derivatives read the ring;
 //   * the mixed second derivatives of the stress divergence use, for each i,
 //       sum_{j != i} d2 u_j/dx_i dx_j = D1_i( s_i ),  s_i = sum_{j != i} D1_j u_j,
@@ -29,6 +34,7 @@
 // only through the reference enthalpy term -H0 div u).
 #pragma once
 
+#include "fpconv.cuh"
 #include "sbli_internal.cuh"
 
 namespace sbli {
@@ -38,13 +44,13 @@ constexpr int HALO = 2;
 constexpr int SX = TX + 2 * HALO;
 constexpr int NSLOT = 5;
 
-// primitive values kept per point in a ring slot
+// primitive values of one point record in a ring slot
 enum { V_RHO, V_M0, V_M1, V_M2, V_E, V_U0, V_U1, V_U2, V_P, V_T, NV };
 
 template <typename T, int TY>
 struct FusedSmem {
   static constexpr int SY = TY + 2 * HALO;
-  T ring[NSLOT][NV][SY][SX];  // rho', m_i, E', u_i, p', T' per haloed point
+  T ring[NSLOT][SY][SX][NV];  // rho', m_i, E', u_i, p', T' per haloed point
   T dring[NSLOT][2][TY][TX];  // D1_x u0 and D1_y u1 per plane (tile only)
   T s0buf[TY][SX];            // s_0 = D1_y u1 + D1_z u2, centre plane, x0-haloed rows
   T s1buf[SY][TX];            // s_1 = D1_x u0 + D1_z u2, centre plane, x1-haloed columns
@@ -57,6 +63,48 @@ template <>
 __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
 template <>
 __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+
+// Record load/store with 8-byte (binary32: 40-byte records) or 16-byte
+// (binary64: 80-byte records) vector accesses.
+__device__ __forceinline__ void load_rec(const float* p, float (&r)[NV]) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) {
+    const float2 t = q[i];
+    r[2 * i] = t.x;
+    r[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void load_rec(const double* p, double (&r)[NV]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) {
+    const double2 t = q[i];
+    r[2 * i] = t.x;
+    r[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void store_rec(float* p, const float (&r)[NV]) {
+  float2* q = reinterpret_cast<float2*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) q[i] = make_float2(r[2 * i], r[2 * i + 1]);
+}
+__device__ __forceinline__ void store_rec(double* p, const double (&r)[NV]) {
+  double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) q[i] = make_double2(r[2 * i], r[2 * i + 1]);
+}
+
+// Stage input value in the arithmetic type (binary64 inputs to a binary32
+// stage are narrowed with integer re-packing, see fpconv.cuh).
+template <typename T, typename TIN>
+__device__ __forceinline__ T to_compute(TIN v) {
+  return T(v);
+}
+template <>
+__device__ __forceinline__ float to_compute<float, double>(double v) {
+  return narrow_f64_fast(v);
+}
 
 // Accumulated terms of the residual at one point.
 template <typename T>
@@ -72,65 +120,56 @@ struct Terms {
   T G[3];      // sum_j d2 u_j / dx_i dx_j (Eq. 7 on j = i, D1 o D1 otherwise)
 };
 
-// All derivatives along axis A at one point.  nb(v, k) returns primitive v
-// at the neighbour k = 0..3 (offsets -2, -1, +1, +2 along A); uc, Tc are the
+// All derivatives along axis A at one point.  nbp(k) points at the record of
+// the neighbour k = 0..3 (offsets -2, -1, +1, +2 along A); uc, Tc are the
 // centre values; s[k] the mixed-term helper s_A at the neighbours.
-template <int A, typename T, typename NB>
-__device__ __forceinline__ void axis_terms(const NB& nb, const T (&s)[4], const Coef<T>& c, const T (&uc)[3], T Tc,
+template <int A, typename T, typename NBP>
+__device__ __forceinline__ void axis_terms(const NBP& nbp, const T (&s)[4], const Coef<T>& c, const T (&uc)[3], T Tc,
                                            Terms<T>& t) {
   const T c1 = c.c1[A], c2 = c.c2[A], e0 = c.e0[A], e1 = c.e1[A], e2 = c.e2[A];
   auto d1 = [&](T fm2, T fm1, T fp1, T fp2) { return c1 * (fp1 - fm1) - c2 * (fp2 - fm2); };
   auto d2 = [&](T fm2, T fm1, T f0, T fp1, T fp2) { return e0 * f0 + e1 * (fp1 + fm1) + e2 * (fp2 + fm2); };
 
-  T rho[4], m[3][4], E[4], u[3][4], p[4], Tt[4];
+  T r[4][NV];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    rho[k] = nb(V_RHO, k);
-    m[0][k] = nb(V_M0, k);
-    m[1][k] = nb(V_M1, k);
-    m[2][k] = nb(V_M2, k);
-    E[k] = nb(V_E, k);
-    u[0][k] = nb(V_U0, k);
-    u[1][k] = nb(V_U1, k);
-    u[2][k] = nb(V_U2, k);
-    p[k] = nb(V_P, k);
-    Tt[k] = nb(V_T, k);
-  }
+  for (int k = 0; k < 4; ++k) load_rec(nbp(k), r[k]);
+#define SBLI_D1(V) d1(r[0][V], r[1][V], r[2][V], r[3][V])
   const T ua = uc[A];
-  const T Drho = d1(rho[0], rho[1], rho[2], rho[3]);
-  const T DE = d1(E[0], E[1], E[2], E[3]);
+  const T Drho = SBLI_D1(V_RHO);
+  const T DE = SBLI_D1(V_E);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T Dm = d1(m[i][0], m[i][1], m[i][2], m[i][3]);
+    const T Dm = SBLI_D1(V_M0 + i);
     if (i == A) {
       t.rrho += Dm + ua * Drho;
       t.rm[i] += ua * Dm;
       T P[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) P[k] = T(0.5) * m[A][k] * u[A][k] + p[k];
+      for (int k = 0; k < 4; ++k) P[k] = T(0.5) * r[k][V_M0 + A] * r[k][V_U0 + A] + r[k][V_P];
       t.rmx[i] -= d1(P[0], P[1], P[2], P[3]);
     } else {
       T P[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) P[k] = m[i][k] * u[A][k];
+      for (int k = 0; k < 4; ++k) P[k] = r[k][V_M0 + i] * r[k][V_U0 + A];
       t.rm[i] += d1(P[0], P[1], P[2], P[3]) + ua * Dm;
-      t.g[i][A] = d1(u[i][0], u[i][1], u[i][2], u[i][3]);
+      t.g[i][A] = SBLI_D1(V_U0 + i);
     }
   }
   {
     T PE[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) PE[k] = (T(0.5) * E[k] + p[k]) * u[A][k];
+    for (int k = 0; k < 4; ++k) PE[k] = (T(0.5) * r[k][V_E] + r[k][V_P]) * r[k][V_U0 + A];
     t.rE1 += d1(PE[0], PE[1], PE[2], PE[3]);
   }
   t.rE2 += ua * DE;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T l = d2(u[i][0], u[i][1], uc[i], u[i][2], u[i][3]);
+    const T l = d2(r[0][V_U0 + i], r[1][V_U0 + i], uc[i], r[2][V_U0 + i], r[3][V_U0 + i]);
     t.lap[i] += l;
     if (i == A) t.G[A] = l + d1(s[0], s[1], s[2], s[3]);
   }
-  t.lapT += d2(Tt[0], Tt[1], Tc, Tt[2], Tt[3]);
+  t.lapT += d2(r[0][V_T], r[1][V_T], Tc, r[2][V_T], r[3][V_T]);
+#undef SBLI_D1
 }
 
 // TIN: type of the stage input in HBM; TOUT: type of the stage output.
@@ -146,8 +185,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
   S& sm = *reinterpret_cast<S*>(smem_raw);
 
   const int n0 = a.g.n0, n1 = a.g.n1, n2 = a.g.n2;
-  const long long P = a.g.P;
-  const long long plane = (long long)n0 * n1;
+  const unsigned plane = (unsigned)n0 * (unsigned)n1;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -155,8 +193,15 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
   const int zend = min(zbeg + a.zc, n2);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid_xy = (gx < n0) && (gy < n1);
-  const long long own_off = valid_xy ? (gx + (long long)n0 * gy) : 0;
-  const TIN* __restrict__ qin = static_cast<const TIN*>(a.q_in);
+  const unsigned own_off = valid_xy ? (unsigned)gx + (unsigned)n0 * (unsigned)gy : 0u;
+  // per-field base pointers; offsets inside a field are 32-bit (P < 2^32)
+  const TIN* qf[NF];
+  const double* accf[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    qf[f] = static_cast<const TIN*>(a.q_in) + (long long)f * a.g.P;
+    accf[f] = a.acc_in ? a.acc_in + (long long)f * a.g.P : nullptr;
+  }
 
   // haloed points this thread loads on every plane (periodic wrap)
   int ld_off[LPT], ld_s[LPT];
@@ -166,7 +211,7 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
     if (idx < PTS) {
       const int sy = idx / SX, sx = idx % SX;
       ld_off[l] = wrapi(x0 - HALO + sx, n0) + n0 * wrapi(y0 - HALO + sy, n1);
-      ld_s[l] = sy * SX + sx;
+      ld_s[l] = idx;
     } else {
       ld_off[l] = -1;
       ld_s[l] = 0;
@@ -175,55 +220,70 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
 
   double ke_acc = 0.0, ens_acc = 0.0;
   const int nplanes = zend - zbeg;
+  const int nit = nplanes + 4;
   T d22 = T(0);
 
-  for (int it = 0; it < nplanes + 4; ++it) {
+  TIN pf[LPT][NF];
+  auto issue_loads = [&](int it_load) {
+    const unsigned zoff = (unsigned)wrapi(zbeg - HALO + it_load, n2) * plane;
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+      if (ld_off[l] >= 0) {
+        const unsigned o = zoff + (unsigned)ld_off[l];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) pf[l][f] = qf[f][o];
+      }
+    }
+  };
+  issue_loads(0);
+
+  for (int it = 0; it < nit; ++it) {
     // ---------------------------------------------------------------- phase 1
-    // plane e = zbeg - 2 + it enters slot it % 5: load Q', derive primitives
-    // (Eqs. 4-5 in deviation form) on the haloed tile.
+    // plane e = zbeg - 2 + it enters slot it % 5: derive primitives (Eqs. 4-5
+    // in deviation form) on the haloed tile from the prefetched Q'.
     const int se = it % NSLOT;
     {
-      const long long zoff = (long long)wrapi(zbeg - HALO + it, n2) * plane;
       T* ring = &sm.ring[se][0][0][0];
-      constexpr int PL = SY * SX;
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
         if (ld_off[l] >= 0) {
-          const long long o = zoff + ld_off[l];
-          const T rho_p = T(qin[o]);
-          const T m0 = T(qin[P + o]);
-          const T m1 = T(qin[2 * P + o]);
-          const T m2 = T(qin[3 * P + o]);
-          const T E_p = T(qin[4 * P + o]);
+          T rec[NV];
+          const T rho_p = to_compute<T, TIN>(pf[l][0]);
+          const T m0 = to_compute<T, TIN>(pf[l][1]);
+          const T m1 = to_compute<T, TIN>(pf[l][2]);
+          const T m2 = to_compute<T, TIN>(pf[l][3]);
+          const T E_p = to_compute<T, TIN>(pf[l][4]);
           const T rinv = rcp_rn<T>(T(1) + rho_p);
           const T u0 = m0 * rinv, u1 = m1 * rinv, u2 = m2 * rinv;
           const T mu = m0 * u0 + m1 * u1 + m2 * u2;
-          const T p_p = c.gm1 * (E_p - T(0.5) * mu);          // Eq. 4: p - p_ref
-          const T T_p = (c.gM2 * p_p - rho_p) * rinv;         // Eq. 5: T - 1
-          const int s = ld_s[l];
-          ring[V_RHO * PL + s] = rho_p;
-          ring[V_M0 * PL + s] = m0;
-          ring[V_M1 * PL + s] = m1;
-          ring[V_M2 * PL + s] = m2;
-          ring[V_E * PL + s] = E_p;
-          ring[V_U0 * PL + s] = u0;
-          ring[V_U1 * PL + s] = u1;
-          ring[V_U2 * PL + s] = u2;
-          ring[V_P * PL + s] = p_p;
-          ring[V_T * PL + s] = T_p;
+          const T p_p = c.gm1 * (E_p - T(0.5) * mu);   // Eq. 4: p - p_ref
+          const T T_p = (c.gM2 * p_p - rho_p) * rinv;  // Eq. 5: T - 1
+          rec[V_RHO] = rho_p;
+          rec[V_M0] = m0;
+          rec[V_M1] = m1;
+          rec[V_M2] = m2;
+          rec[V_E] = E_p;
+          rec[V_U0] = u0;
+          rec[V_U1] = u1;
+          rec[V_U2] = u2;
+          rec[V_P] = p_p;
+          rec[V_T] = T_p;
+          store_rec(ring + ld_s[l] * NV, rec);
         }
       }
     }
+    if (it + 1 < nit) issue_loads(it + 1);
     __syncthreads();
     // --------------------------------------------------------------- phase 2a
     // in-plane diagonal gradients of the entering plane, kept for s_2 and
     // for the velocity gradient when the plane is the centre.
     {
-      const T(*U0)[SX] = sm.ring[se][V_U0];
-      const T(*U1)[SX] = sm.ring[se][V_U1];
+      const T(*R)[SX][NV] = sm.ring[se];
       const int sy = ty + HALO, sx = tx + HALO;
-      sm.dring[se][0][ty][tx] = c.c1[0] * (U0[sy][sx + 1] - U0[sy][sx - 1]) - c.c2[0] * (U0[sy][sx + 2] - U0[sy][sx - 2]);
-      sm.dring[se][1][ty][tx] = c.c1[1] * (U1[sy + 1][sx] - U1[sy - 1][sx]) - c.c2[1] * (U1[sy + 2][sx] - U1[sy - 2][sx]);
+      sm.dring[se][0][ty][tx] = c.c1[0] * (R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0]) -
+                                c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]);
+      sm.dring[se][1][ty][tx] = c.c1[1] * (R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1]) -
+                                c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]);
     }
     if (it < 4) continue;  // ring not yet full; slots written so far are not read again before the next sync
 
@@ -233,33 +293,42 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
 #pragma unroll
     for (int o = 0; o < 5; ++o) sl[o] = (it + 1 + o) % NSLOT;
     const int scen = sl[2];
+    const unsigned o_own = (unsigned)zc * plane + own_off;
+
+    // accumulator of the centre point, fetched before the arithmetic
+    double accv[NF];
+    if (!RHS_ONLY && valid_xy) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) accv[f] = accf[f] ? accf[f][o_own] : double(qf[f][o_own]);
+    }
 
     // --------------------------------------------------------------- phase 2b
     // s_0 and s_1 on the centre plane's tile and halo.
     {
       const int sy = ty + HALO, sx = tx + HALO;
       auto u2z = [&](int yy, int xx) {
-        return c.c1[2] * (sm.ring[sl[3]][V_U2][yy][xx] - sm.ring[sl[1]][V_U2][yy][xx]) -
-               c.c2[2] * (sm.ring[sl[4]][V_U2][yy][xx] - sm.ring[sl[0]][V_U2][yy][xx]);
+        return c.c1[2] * (sm.ring[sl[3]][yy][xx][V_U2] - sm.ring[sl[1]][yy][xx][V_U2]) -
+               c.c2[2] * (sm.ring[sl[4]][yy][xx][V_U2] - sm.ring[sl[0]][yy][xx][V_U2]);
       };
       d22 = u2z(sy, sx);
       sm.s0buf[ty][sx] = sm.dring[scen][1][ty][tx] + d22;
       sm.s1buf[sy][tx] = sm.dring[scen][0][ty][tx] + d22;
-      const T(*U0)[SX] = sm.ring[scen][V_U0];
-      const T(*U1)[SX] = sm.ring[scen][V_U1];
+      const T(*R)[SX][NV] = sm.ring[scen];
       for (int h = tid; h < 4 * (TX + TY); h += NT) {
         if (h < 4 * TY) {
           const int r = h >> 2, k = h & 3;
           const int hx = (k < 2) ? k : TX + k;  // 0, 1, TX+2, TX+3
           const int hy = r + HALO;
-          const T d11 = c.c1[1] * (U1[hy + 1][hx] - U1[hy - 1][hx]) - c.c2[1] * (U1[hy + 2][hx] - U1[hy - 2][hx]);
+          const T d11 = c.c1[1] * (R[hy + 1][hx][V_U1] - R[hy - 1][hx][V_U1]) -
+                        c.c2[1] * (R[hy + 2][hx][V_U1] - R[hy - 2][hx][V_U1]);
           sm.s0buf[r][hx] = d11 + u2z(hy, hx);
         } else {
           const int h2 = h - 4 * TY;
           const int col = h2 % TX, k = h2 / TX;
           const int hy = (k < 2) ? k : TY + k;
           const int hx = col + HALO;
-          const T d00 = c.c1[0] * (U0[hy][hx + 1] - U0[hy][hx - 1]) - c.c2[0] * (U0[hy][hx + 2] - U0[hy][hx - 2]);
+          const T d00 = c.c1[0] * (R[hy][hx + 1][V_U0] - R[hy][hx - 1][V_U0]) -
+                        c.c2[0] * (R[hy][hx + 2][V_U0] - R[hy][hx - 2][V_U0]);
           sm.s1buf[hy][col] = d00 + u2z(hy, hx);
         }
       }
@@ -268,12 +337,14 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
     // ---------------------------------------------------------------- phase 3
     {
       const int sy = ty + HALO, sx = tx + HALO;
-      const T(*C)[SY][SX] = sm.ring[scen];
-      const T rho_p = C[V_RHO][sy][sx];
-      const T mc[3] = {C[V_M0][sy][sx], C[V_M1][sy][sx], C[V_M2][sy][sx]};
-      const T Ec = C[V_E][sy][sx];
-      const T uc[3] = {C[V_U0][sy][sx], C[V_U1][sy][sx], C[V_U2][sy][sx]};
-      const T Tc = C[V_T][sy][sx];
+      const T(*C)[SX][NV] = sm.ring[scen];
+      T cen[NV];
+      load_rec(&C[sy][sx][0], cen);
+      const T rho_p = cen[V_RHO];
+      const T mc[3] = {cen[V_M0], cen[V_M1], cen[V_M2]};
+      const T Ec = cen[V_E];
+      const T uc[3] = {cen[V_U0], cen[V_U1], cen[V_U2]};
+      const T Tc = cen[V_T];
 
       Terms<T> t;
       t.rrho = T(0);
@@ -288,26 +359,26 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
       t.g[1][1] = sm.dring[scen][1][ty][tx];
       t.g[2][2] = d22;
 
-      // x0: velocity component 0 group first (SN2 ordering), then x1, x2
+      // x0 group first (SN2 ordering), then x1, x2
       {
         const T s[4] = {sm.s0buf[ty][sx - 2], sm.s0buf[ty][sx - 1], sm.s0buf[ty][sx + 1], sm.s0buf[ty][sx + 2]};
         const int off[4] = {-2, -1, 1, 2};
-        auto nb = [&](int v, int k) { return C[v][sy][sx + off[k]]; };
-        axis_terms<0>(nb, s, c, uc, Tc, t);
+        auto nbp = [&](int k) { return &C[sy][sx + off[k]][0]; };
+        axis_terms<0>(nbp, s, c, uc, Tc, t);
       }
       {
         const T s[4] = {sm.s1buf[sy - 2][tx], sm.s1buf[sy - 1][tx], sm.s1buf[sy + 1][tx], sm.s1buf[sy + 2][tx]};
         const int off[4] = {-2, -1, 1, 2};
-        auto nb = [&](int v, int k) { return C[v][sy + off[k]][sx]; };
-        axis_terms<1>(nb, s, c, uc, Tc, t);
+        auto nbp = [&](int k) { return &C[sy + off[k]][sx][0]; };
+        axis_terms<1>(nbp, s, c, uc, Tc, t);
       }
       {
         const int zs[4] = {sl[0], sl[1], sl[3], sl[4]};
         T s[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) s[k] = sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx];
-        auto nb = [&](int v, int k) { return sm.ring[zs[k]][v][sy][sx]; };
-        axis_terms<2>(nb, s, c, uc, Tc, t);
+        auto nbp = [&](int k) { return &sm.ring[zs[k]][sy][sx][0]; };
+        axis_terms<2>(nbp, s, c, uc, Tc, t);
       }
 
       // assemble Eqs. 1-3
@@ -329,17 +400,28 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
       R[4] = -t.rE1 - T(0.5) * (t.rE2 + Ec * div) - c.H0 * div + c.inv_re * (uvisc + diss) + c.kappa * t.lapT;
 
       if (valid_xy) {
-        const long long o = (long long)zc * plane + own_off;
         if (RHS_ONLY) {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) a.r_out[f * P + o] = double(R[f]);
-        } else {
+          for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o_own] = double(R[f]);
+        } else if (sizeof(T) == 8) {
+          // binary64 stage: acc + b dt R and acc + a dt R, fused multiply-adds
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            const double accv = a.acc_in ? a.acc_in[f * P + o] : double(qin[f * P + o]);
             const double r = double(R[f]);
-            a.acc_out[f * P + o] = fma(a.b_dt, r, accv);
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[f * P + o] = TOUT(fma(a.a_dt, r, accv));
+            a.acc_out[(long long)f * a.g.P + o_own] = fma(a.b_dt, r, accv[f]);
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(fma(a.a_dt, r, accv[f]));
+          }
+        } else {
+          // binary32 stage, binary64 accumulator: one DADD per field,
+          //   acc' = acc + (b dt R),  Q_{k+1} = float(acc') + (a - b) dt R
+          // (conversions by integer re-packing, fpconv.cuh)
+          const float bdt = float(a.b_dt), ambdt = float(a.amb_dt);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const float r = float(R[f]);
+            const double accn = accv[f] + widen_f32_fast(bdt * r);
+            a.acc_out[(long long)f * a.g.P + o_own] = accn;
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(narrow_f64_fast(accn) + ambdt * r);
           }
         }
         if (WITH_KE) {

@@ -65,6 +65,7 @@ struct StageArgs {
   void* q_out;             // stage output, nullptr on the last stage
   double* r_out;           // RHS-only mode: R (binary64)
   double a_dt, b_dt;       // a_k dt, b_k dt
+  double amb_dt;           // (a_k - b_k) dt
   double* ke_partials;     // per-CTA (ke, enstrophy) partial sums, or nullptr
 };
 
