@@ -164,6 +164,52 @@ SBLI_API int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev);
 SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, int n2, double L, double* out_dev,
                                          void* stream);
 
+/* Launch configuration of the fused kernel: in-plane tile height (the tile
+ * is 32 x tile_y points; binary64 grids use 8, binary32 grids 8 or 16) and
+ * planes per CTA along x2 (>= 4).  set_config validates and applies it
+ * (cached step graphs are rebuilt); must be called at a step boundary. */
+SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta);
+SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta);
+
+/* Autotuner: times candidate configurations (each allowed tile height with
+ * the planes-per-CTA values a wave-balance model ranks best) on this grid with
+ * `reps` timed stage-0 launches each, which read the state and write only the
+ * scratch registers, keeps the fastest and returns it.  The state is not
+ * changed.  Synchronises the grid's stream.  Fused variant only. */
+SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, float* best_stage_ms);
+
+/* ---------------------------------------------------------------------
+ * Batched ensembles: up to 64 members (each its own grid size, Re, M, Pr,
+ * gamma, L) advanced together.  Every Runge-Kutta stage of all members is one
+ * persistent kernel launch that walks the members' work items (z chunk x
+ * 32 x 8 tile); step loops are captured as CUDA graphs.  Precision as for
+ * single grids.  Members' results are bitwise those of the same member run
+ * alone as a single grid with tile height 8.
+ * n: 3*count edge lengths (n0, n1, n2 per member); params: count entries.
+ * --------------------------------------------------------------------- */
+typedef struct sbli_batch sbli_batch;
+
+SBLI_API int sbli_batch_workspace_bytes(int count, const int* n, int precision, size_t* bytes);
+SBLI_API int sbli_batch_create(sbli_batch** out, int count, const int* n, const sbli_params* params, int precision,
+                               void* workspace, size_t workspace_bytes, void* stream);
+SBLI_API int sbli_batch_destroy(sbli_batch* b);
+SBLI_API int sbli_batch_count(const sbli_batch* b, int* count);
+/* Total work items of one stage (for scheduling diagnostics). */
+SBLI_API int sbli_batch_work_items(const sbli_batch* b, long long* items);
+/* Taylor-Green initial field per member with amplitudes[count]. */
+SBLI_API int sbli_batch_init_tgv(sbli_batch* b, const double* amplitudes);
+/* Member state in/out as plain binary64 conserved variables (as sbli_set_state). */
+SBLI_API int sbli_batch_set_state(sbli_batch* b, int member, const double* q, int q_is_host);
+SBLI_API int sbli_batch_get_state(sbli_batch* b, int member, double* q, int q_is_host);
+/* nsteps time steps of every member with time step dt.  Asynchronous. */
+SBLI_API int sbli_batch_step_n(sbli_batch* b, int nsteps, double dt);
+/* As sbli_batch_step_n, writing (ke, enstrophy) of every member before each
+ * step s at ke_hist_dev[2*(count*s + m)] (device, 2*count*nsteps binary64). */
+SBLI_API int sbli_batch_step_n_history(sbli_batch* b, int nsteps, double dt, double* ke_hist_dev);
+/* Per-member volume averages (binary64) into host arrays ke[count],
+ * enstrophy[count].  Synchronises the batch's stream. */
+SBLI_API int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstrophy);
+
 /* Number of stages completed since creation or the last set_state/init. */
 SBLI_API int sbli_stage_count(const sbli_grid* g, long long* stages);
 

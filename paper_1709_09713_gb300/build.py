@@ -37,7 +37,7 @@ def sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".map"))]
     files.append(os.path.join(INCLUDE, "sbli.h"))
     return files
 
@@ -71,7 +71,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    exports = os.path.join(CSRC, "exports.map")
+    r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-Xlinker", f"--version-script={exports}"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -115,32 +115,55 @@ struct sbli_grid {
 
 namespace {
 
-FusedConfig default_config(const Geom& g, int precision) {
-  // Tile 32 x 8; choose planes per CTA to balance waves over 152 SMs: cost
-  // model = waves * (zc + 1.5) (the 4 prologue planes cost about 1.5 full
-  // planes of work), minimised over zc.
-  FusedConfig cfg;
-  cfg.ty = 8;
+// CTAs per SM a tile height allows (shared memory bound).
+int ctas_per_sm(int precision, int ty) { return (precision == SBLI_FP64 || ty >= 16) ? 1 : 2; }
+
+// Planes per CTA ranked by a wave-balance model: cost = waves * (zc + 1.5),
+// the 4 warm-up planes of a z segment costing about 1.5 full planes.
+void rank_zc(const Geom& g, int precision, int ty, int* best, int nbest) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = precision == SBLI_FP64 ? 1 : 2;
-  const long long slots = (long long)sms * per_sm;
-  const long long tiles = (long long)((g.n0 + 31) / 32) * ((g.n1 + cfg.ty - 1) / cfg.ty);
-  double best = 1e300;
-  int best_zc = g.n2;
+  const long long slots = (long long)sms * ctas_per_sm(precision, ty);
+  const long long tiles = (long long)((g.n0 + 31) / 32) * ((g.n1 + ty - 1) / ty);
+  double cost[8];
+  for (int i = 0; i < nbest; ++i) {
+    best[i] = 0;
+    cost[i] = 1e300;
+  }
   for (int zc = 4; zc <= g.n2; ++zc) {
     const long long gz = (g.n2 + zc - 1) / zc;
-    if ((gz - 1) * zc >= g.n2) continue;  // same gz as a smaller zc
-    const long long ctas = tiles * gz;
-    const long long waves = (ctas + slots - 1) / slots;
-    const double cost = (double)waves * (zc + 1.5);
-    if (cost < best - 1e-9) {
-      best = cost;
-      best_zc = zc;
+    if (zc > 4 && (gz - 1) * zc >= g.n2) continue;  // same CTA count as a smaller zc
+    const long long waves = (tiles * gz + slots - 1) / slots;
+    const double c = (double)waves * (zc + 1.5);
+    for (int i = 0; i < nbest; ++i) {
+      if (c < cost[i] - 1e-9) {
+        for (int j = nbest - 1; j > i; --j) {
+          cost[j] = cost[j - 1];
+          best[j] = best[j - 1];
+        }
+        cost[i] = c;
+        best[i] = zc;
+        break;
+      }
     }
   }
-  cfg.zc = std::max(4, std::min(best_zc, g.n2));
+  for (int i = 0; i < nbest; ++i)
+    if (best[i] == 0) best[i] = best[0] ? best[0] : std::min(4, g.n2);
+}
+
+FusedConfig default_config(const Geom& g, int precision) {
+  FusedConfig cfg;
+  cfg.ty = 8;
+  int zc[1];
+  rank_zc(g, precision, cfg.ty, zc, 1);
+  cfg.zc = std::max(4, std::min(zc[0], g.n2));
   return cfg;
+}
+
+bool valid_config(int precision, int ty, int zc) {
+  if (zc < 4) return false;
+  if (precision == SBLI_FP64) return ty == 8;
+  return ty == 8 || ty == 16;
 }
 
 // Pointers of stage k for the current rotation.
@@ -522,6 +545,88 @@ int sbli_kinetic_energy(sbli_grid* g, double* ke, double* enstrophy) {
   SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
   *ke = h[0];
   *enstrophy = h[1];
+  return SBLI_OK;
+}
+
+int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta) {
+  if (!g || !tile_y || !planes_per_cta) return fail(SBLI_EINVAL, "null argument");
+  *tile_y = g->cfg.ty;
+  *planes_per_cta = g->cfg.zc;
+  return SBLI_OK;
+}
+
+int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta) {
+  if (int rc = check_grid(g)) return rc;
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "set_config between stages of a step");
+  if (!valid_config(g->precision, tile_y, planes_per_cta))
+    return fail(SBLI_EINVAL, "config tile_y=%d planes_per_cta=%d not available for this precision", tile_y,
+                planes_per_cta);
+  FusedConfig cfg;
+  cfg.ty = tile_y;
+  cfg.zc = std::min(planes_per_cta, g->geom.n2);
+  if (cfg.ty != g->cfg.ty || cfg.zc != g->cfg.zc) {
+    g->cfg = cfg;
+    drop_graphs(g);
+  }
+  return SBLI_OK;
+}
+
+int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, float* best_stage_ms) {
+  if (int rc = check_grid(g)) return rc;
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "autotune between stages of a step");
+  if (g->variant != SBLI_FUSED) return fail(SBLI_EUNSUPPORTED, "autotune needs the fused variant");
+  if (reps < 1) return fail(SBLI_EINVAL, "reps must be >= 1");
+  FusedConfig cand[8];
+  int nc = 0;
+  const int tys[2] = {8, 16};
+  for (int t = 0; t < 2; ++t) {
+    if (!valid_config(g->precision, tys[t], 4)) continue;
+    int zc[3];
+    rank_zc(g->geom, g->precision, tys[t], zc, 3);
+    for (int i = 0; i < 3; ++i) {
+      bool dup = false;
+      for (int j = 0; j < nc; ++j) dup |= (cand[j].ty == tys[t] && cand[j].zc == zc[i]);
+      if (!dup && nc < 8) cand[nc++] = FusedConfig{tys[t], std::max(4, std::min(zc[i], g->geom.n2))};
+    }
+  }
+  cudaEvent_t e0, e1;
+  SBLI_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "cudaEventCreate");
+  }
+  const FusedConfig saved = g->cfg;
+  int best = -1;
+  float best_ms = 1e30f;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < nc && err == cudaSuccess; ++i) {
+    g->cfg = cand[i];
+    // stage 0 reads the state and writes only the two other registers
+    err = enqueue_stage(g, 0, g->state, 1e-6, nullptr, g->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, g->stream);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = enqueue_stage(g, 0, g->state, 1e-6, nullptr, g->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, g->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (err == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    g->cfg = saved;
+    return cuda_fail(err, "autotune launch");
+  }
+  g->cfg = cand[best];
+  if (g->cfg.ty != saved.ty || g->cfg.zc != saved.zc) drop_graphs(g);
+  if (tile_y) *tile_y = g->cfg.ty;
+  if (planes_per_cta) *planes_per_cta = g->cfg.zc;
+  if (best_stage_ms) *best_stage_ms = best_ms;
   return SBLI_OK;
 }
 

@@ -1,6 +1,7 @@
 // fused_fp32.cu -- binary32 instantiations of the fused stage kernel.  The
 // stage input is binary64 at stage 0 (the state between steps) and binary32
-// at stages 1-2; the accumulator is always binary64.
+// at stages 1-2; the accumulator is always binary64.  Tiles 32 x 8 (two CTAs
+// per SM) and 32 x 16 (one CTA of 16 warps per SM).
 #include "fused_stage.cuh"
 
 namespace sbli {
@@ -22,8 +23,8 @@ static cudaError_t dispatch32(const StageArgs& a, const Coef<float>& c, bool in_
 cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                               bool rhs_only, cudaStream_t s) {
   switch (cfg.ty) {
-    case 4: return dispatch32<4>(a, c, in_fp64, rhs_only, s);
     case 8: return dispatch32<8>(a, c, in_fp64, rhs_only, s);
+    case 16: return dispatch32<16>(a, c, in_fp64, rhs_only, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -34,8 +35,8 @@ int fused_num_ctas(const Geom& g, const FusedConfig& cfg) {
 }
 
 size_t fused_smem_bytes(int elem_bytes, int ty) {
-  if (elem_bytes == 8) return ty == 4 ? sizeof(FusedSmem<double, 4>) : sizeof(FusedSmem<double, 8>);
-  return ty == 4 ? sizeof(FusedSmem<float, 4>) : sizeof(FusedSmem<float, 8>);
+  if (elem_bytes == 8) return sizeof(FusedSmem<double, 8>);
+  return ty == 16 ? sizeof(FusedSmem<float, 16>) : sizeof(FusedSmem<float, 8>);
 }
 
 }  // namespace sbli

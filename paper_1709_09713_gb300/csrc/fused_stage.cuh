@@ -65,7 +65,8 @@ template <>
 __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
 
 // Record load/store with 8-byte (binary32: 40-byte records) or 16-byte
-// (binary64: 80-byte records) vector accesses.
+// (binary64: 80-byte records) vector accesses; both strides are bank-conflict
+// free for the vector width used.
 __device__ __forceinline__ void load_rec(const float* p, float (&r)[NV]) {
   const float2* q = reinterpret_cast<const float2*>(p);
 #pragma unroll
@@ -106,91 +107,96 @@ __device__ __forceinline__ float to_compute<float, double>(double v) {
   return narrow_f64_fast(v);
 }
 
-// Accumulated terms of the residual at one point.
+// Accumulated terms of the residual at one point.  By linearity of D1 and
+// because the centre values u_j^c are constants over a stencil, the
+// convective and skew terms of Eqs. 1-3 combine into single derivatives:
+//   D_j(m_i u_j) + u_j^c D_j m_i       = D_j( m_i (u_j + u_j^c) )
+//   D_j m_j + u_j^c D_j rho'            = D_j( m_j + u_j^c rho' )
+//   D_j(E' u_j) + u_j^c D_j E'          = D_j( E' (u_j + u_j^c) )
 template <typename T>
 struct Terms {
   T g[3][3];   // g[i][j] = D1_j u_i
-  T rrho;      // sum_j D_j m_j + u_j D_j rho'                    (Eq. 1 without rho div u)
-  T rm[3];     // sum_{j != i} D_j(m_i u_j) + u_j D_j m_i         (Eq. 2 without m_i div u)
-  T rmx[3];    // -D_i(m_i u_i / 2 + p')                          (Eq. 2 diagonal product + pressure)
-  T rE1;       // sum_j D_j((E'/2 + p') u_j)                      (Eq. 3 E'u and p'u fluxes)
-  T rE2;       // sum_j u_j D_j E'
-  T lap[3];    // sum_j D2_j u_i
-  T lapT;      // sum_j D2_j T'
+  T rrho;      // sum_j D_j(m_j + u_j^c rho')                     (Eq. 1 without rho div u)
+  T rM[3];     // sum_j D_j(m_i (u_j + u_j^c)) + 2 D_i p'          (Eq. 2 without m_i div u)
+  T rE;        // sum_j D_j(E' (u_j + u_j^c)) + 2 D_j(p' u_j)      (Eq. 3 without E' div u)
+  T lap[3];    // sum_j D2_j u_i, off-centre part
+  T lapT;      // sum_j D2_j T', off-centre part
   T G[3];      // sum_j d2 u_j / dx_i dx_j (Eq. 7 on j = i, D1 o D1 otherwise)
 };
 
 // All derivatives along axis A at one point.  nbp(k) points at the record of
-// the neighbour k = 0..3 (offsets -2, -1, +1, +2 along A); uc, Tc are the
-// centre values; s[k] the mixed-term helper s_A at the neighbours.
-template <int A, typename T, typename NBP>
-__device__ __forceinline__ void axis_terms(const NBP& nbp, const T (&s)[4], const Coef<T>& c, const T (&uc)[3], T Tc,
+// the neighbour k = 0..3 (offsets -2, -1, +1, +2 along A); uc are the centre
+// velocities; sfun(k, record) gives the mixed-term helper s_A at neighbour k.
+template <int A, typename T, typename NBP, typename SF>
+__device__ __forceinline__ void axis_terms(const NBP& nbp, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
                                            Terms<T>& t) {
   const T c1 = c.c1[A], c2 = c.c2[A], e0 = c.e0[A], e1 = c.e1[A], e2 = c.e2[A];
   auto d1 = [&](T fm2, T fm1, T fp1, T fp2) { return c1 * (fp1 - fm1) - c2 * (fp2 - fm2); };
-  auto d2 = [&](T fm2, T fm1, T f0, T fp1, T fp2) { return e0 * f0 + e1 * (fp1 + fm1) + e2 * (fp2 + fm2); };
 
   T r[4][NV];
 #pragma unroll
   for (int k = 0; k < 4; ++k) load_rec(nbp(k), r[k]);
+  T s[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] = sfun(k, r[k]);
 #define SBLI_D1(V) d1(r[0][V], r[1][V], r[2][V], r[3][V])
   const T ua = uc[A];
-  const T Drho = SBLI_D1(V_RHO);
-  const T DE = SBLI_D1(V_E);
+  // stencil weights times (u_A + u_A^c):  D1(f w) = f+1 W1 - f-1 V1 - f+2 W2 + f-2 V2
+  const T W1 = c1 * (r[2][V_U0 + A] + ua), V1 = c1 * (r[1][V_U0 + A] + ua);
+  const T W2 = c2 * (r[3][V_U0 + A] + ua), V2 = c2 * (r[0][V_U0 + A] + ua);
+  auto d1w = [&](int V) { return r[2][V] * W1 - r[1][V] * V1 - r[3][V] * W2 + r[0][V] * V2; };
+  // stencil weights times u_A:  D1(f u_A)
+  const T X1 = c1 * r[2][V_U0 + A], Y1 = c1 * r[1][V_U0 + A];
+  const T X2 = c2 * r[3][V_U0 + A], Y2 = c2 * r[0][V_U0 + A];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t.rM[i] += d1w(V_M0 + i);
+  t.rM[A] += T(2) * SBLI_D1(V_P);
+  t.rE += d1w(V_E) + T(2) * (r[2][V_P] * X1 - r[1][V_P] * Y1 - r[3][V_P] * X2 + r[0][V_P] * Y2);
+  t.rrho += d1(fma(ua, r[0][V_RHO], r[0][V_M0 + A]), fma(ua, r[1][V_RHO], r[1][V_M0 + A]),
+               fma(ua, r[2][V_RHO], r[2][V_M0 + A]), fma(ua, r[3][V_RHO], r[3][V_M0 + A]));
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T Dm = SBLI_D1(V_M0 + i);
+    const T off = e1 * (r[2][V_U0 + i] + r[1][V_U0 + i]) + e2 * (r[3][V_U0 + i] + r[0][V_U0 + i]);
+    t.lap[i] += off;
     if (i == A) {
-      t.rrho += Dm + ua * Drho;
-      t.rm[i] += ua * Dm;
-      T P[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) P[k] = T(0.5) * r[k][V_M0 + A] * r[k][V_U0 + A] + r[k][V_P];
-      t.rmx[i] -= d1(P[0], P[1], P[2], P[3]);
+      t.G[A] = fma(e0, uc[A], off) + d1(s[0], s[1], s[2], s[3]);
     } else {
-      T P[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) P[k] = r[k][V_M0 + i] * r[k][V_U0 + A];
-      t.rm[i] += d1(P[0], P[1], P[2], P[3]) + ua * Dm;
       t.g[i][A] = SBLI_D1(V_U0 + i);
     }
   }
-  {
-    T PE[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) PE[k] = (T(0.5) * r[k][V_E] + r[k][V_P]) * r[k][V_U0 + A];
-    t.rE1 += d1(PE[0], PE[1], PE[2], PE[3]);
-  }
-  t.rE2 += ua * DE;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const T l = d2(r[0][V_U0 + i], r[1][V_U0 + i], uc[i], r[2][V_U0 + i], r[3][V_U0 + i]);
-    t.lap[i] += l;
-    if (i == A) t.G[A] = l + d1(s[0], s[1], s[2], s[3]);
-  }
-  t.lapT += d2(r[0][V_T], r[1][V_T], Tc, r[2][V_T], r[3][V_T]);
+  t.lapT += e1 * (r[2][V_T] + r[1][V_T]) + e2 * (r[3][V_T] + r[0][V_T]);
 #undef SBLI_D1
 }
 
 // TIN: type of the stage input in HBM; TOUT: type of the stage output.
+// CTAs per SM the launch bounds plan for: shared memory allows two 32 x 8
+// binary32 CTAs per SM (97.5 KiB each); binary64 (194.5 KiB) and 32 x 16
+// tiles take one.
+template <typename T, int TY>
+constexpr int fused_min_blocks() {
+  return (sizeof(T) == 4 && TY <= 8) ? 2 : 1;
+}
+
+// The z march of one CTA over the 32 x TY column tile (bx, by), output
+// planes [zbeg, min(zend, n2)), for the grid and stage described by `a`.
+// Adds the stage input's kinetic energy and enstrophy of the tile's points
+// to ke_acc / ens_acc when WITH_KE.  Ends with a barrier, so the shared
+// memory can be reused by the caller.
 template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
-__global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
-    fused_stage_kernel(const StageArgs a, const Coef<T> c) {
+__device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c, int bx, int by, int zbeg, int zend_req,
+                                            FusedSmem<T, TY>& sm, double& ke_acc, double& ens_acc) {
   using S = FusedSmem<T, TY>;
   constexpr int SY = S::SY;
   constexpr int NT = TX * TY;
   constexpr int PTS = SX * SY;
   constexpr int LPT = (PTS + NT - 1) / NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S& sm = *reinterpret_cast<S*>(smem_raw);
 
   const int n0 = a.g.n0, n1 = a.g.n1, n2 = a.g.n2;
   const unsigned plane = (unsigned)n0 * (unsigned)n1;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int zbeg = blockIdx.z * a.zc;
-  const int zend = min(zbeg + a.zc, n2);
+  const int x0 = bx * TX, y0 = by * TY;
+  const int zend = min(zend_req, n2);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid_xy = (gx < n0) && (gy < n1);
   const unsigned own_off = valid_xy ? (unsigned)gx + (unsigned)n0 * (unsigned)gy : 0u;
@@ -218,10 +224,41 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
     }
   }
 
-  double ke_acc = 0.0, ens_acc = 0.0;
   const int nplanes = zend - zbeg;
   const int nit = nplanes + 4;
   T d22 = T(0);
+
+  // halo tasks of phase 2b, fixed for the whole z march: s_0 on the x0-halo
+  // columns (4*TY points) and s_1 on the x1-halo rows (4*TX points)
+  constexpr int NHT = 4 * (TX + TY);
+  constexpr int HPT = (NHT + NT - 1) / NT;  // tasks per thread
+  int hk[HPT], hxy[HPT], hdst[HPT];         // kind (0 none, 1 s_0, 2 s_1), packed (hy, hx), buffer index
+#pragma unroll
+  for (int j = 0; j < HPT; ++j) {
+    const int h = tid + j * NT;
+    if (h < 4 * TY) {
+      const int r = h >> 2, k = h & 3;
+      const int hx = (k < 2) ? k : TX + k;  // 0, 1, TX+2, TX+3
+      hk[j] = 1;
+      hxy[j] = ((r + HALO) << 8) | hx;
+      hdst[j] = r * SX + hx;
+    } else if (h < NHT) {
+      const int h2 = h - 4 * TY;
+      const int col = h2 % TX, k = h2 / TX;
+      const int hy = (k < 2) ? k : TY + k;
+      hk[j] = 2;
+      hxy[j] = (hy << 8) | (col + HALO);
+      hdst[j] = hy * TX + col;
+    } else {
+      hk[j] = 0;
+      hxy[j] = 0;
+      hdst[j] = 0;
+    }
+  }
+  // ring slots of planes e-4 .. e (e = entering plane), rotated each iteration
+  int rs[NSLOT];
+#pragma unroll
+  for (int k = 0; k < NSLOT; ++k) rs[k] = (k + 1) % NSLOT;  // any permutation; warm-up fills all slots
 
   TIN pf[LPT][NF];
   auto issue_loads = [&](int it_load) {
@@ -241,7 +278,13 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
     // ---------------------------------------------------------------- phase 1
     // plane e = zbeg - 2 + it enters slot it % 5: derive primitives (Eqs. 4-5
     // in deviation form) on the haloed tile from the prefetched Q'.
-    const int se = it % NSLOT;
+    {
+      const int t0 = rs[0];
+#pragma unroll
+      for (int k = 0; k < NSLOT - 1; ++k) rs[k] = rs[k + 1];
+      rs[NSLOT - 1] = t0;
+    }
+    const int se = rs[NSLOT - 1];
     {
       T* ring = &sm.ring[se][0][0][0];
 #pragma unroll
@@ -280,18 +323,18 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
     {
       const T(*R)[SX][NV] = sm.ring[se];
       const int sy = ty + HALO, sx = tx + HALO;
-      sm.dring[se][0][ty][tx] = c.c1[0] * (R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0]) -
-                                c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]);
-      sm.dring[se][1][ty][tx] = c.c1[1] * (R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1]) -
-                                c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]);
+      const T d00 = c.c1[0] * (R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0]) -
+                    c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]);
+      const T d11 = c.c1[1] * (R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1]) -
+                    c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]);
+      sm.dring[se][0][ty][tx] = d00;
+      sm.dring[se][1][ty][tx] = d11;
     }
     if (it < 4) continue;  // ring not yet full; slots written so far are not read again before the next sync
 
     const int zc = zbeg + it - 4;  // centre plane
     // slot of plane zc + o, o = -2..2
-    int sl[5];
-#pragma unroll
-    for (int o = 0; o < 5; ++o) sl[o] = (it + 1 + o) % NSLOT;
+    const int sl[5] = {rs[0], rs[1], rs[2], rs[3], rs[4]};
     const int scen = sl[2];
     const unsigned o_own = (unsigned)zc * plane + own_off;
 
@@ -314,22 +357,17 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
       sm.s0buf[ty][sx] = sm.dring[scen][1][ty][tx] + d22;
       sm.s1buf[sy][tx] = sm.dring[scen][0][ty][tx] + d22;
       const T(*R)[SX][NV] = sm.ring[scen];
-      for (int h = tid; h < 4 * (TX + TY); h += NT) {
-        if (h < 4 * TY) {
-          const int r = h >> 2, k = h & 3;
-          const int hx = (k < 2) ? k : TX + k;  // 0, 1, TX+2, TX+3
-          const int hy = r + HALO;
+#pragma unroll
+      for (int j = 0; j < HPT; ++j) {
+        const int hy = hxy[j] >> 8, hx = hxy[j] & 0xFF;
+        if (hk[j] == 1) {
           const T d11 = c.c1[1] * (R[hy + 1][hx][V_U1] - R[hy - 1][hx][V_U1]) -
                         c.c2[1] * (R[hy + 2][hx][V_U1] - R[hy - 2][hx][V_U1]);
-          sm.s0buf[r][hx] = d11 + u2z(hy, hx);
-        } else {
-          const int h2 = h - 4 * TY;
-          const int col = h2 % TX, k = h2 / TX;
-          const int hy = (k < 2) ? k : TY + k;
-          const int hx = col + HALO;
+          (&sm.s0buf[0][0])[hdst[j]] = d11 + u2z(hy, hx);
+        } else if (hk[j] == 2) {
           const T d00 = c.c1[0] * (R[hy][hx + 1][V_U0] - R[hy][hx - 1][V_U0]) -
                         c.c2[0] * (R[hy][hx + 2][V_U0] - R[hy][hx - 2][V_U0]);
-          sm.s1buf[hy][col] = d00 + u2z(hy, hx);
+          (&sm.s1buf[0][0])[hdst[j]] = d00 + u2z(hy, hx);
         }
       }
     }
@@ -347,41 +385,38 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
       const T Tc = cen[V_T];
 
       Terms<T> t;
-      t.rrho = T(0);
+      t.rrho = t.rE = t.lapT = T(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        t.rm[i] = T(0);
-        t.rmx[i] = T(0);
+        t.rM[i] = T(0);
         t.lap[i] = T(0);
       }
-      t.rE1 = t.rE2 = t.lapT = T(0);
       t.g[0][0] = sm.dring[scen][0][ty][tx];
       t.g[1][1] = sm.dring[scen][1][ty][tx];
       t.g[2][2] = d22;
 
       // x0 group first (SN2 ordering), then x1, x2
       {
-        const T s[4] = {sm.s0buf[ty][sx - 2], sm.s0buf[ty][sx - 1], sm.s0buf[ty][sx + 1], sm.s0buf[ty][sx + 2]};
         const int off[4] = {-2, -1, 1, 2};
         auto nbp = [&](int k) { return &C[sy][sx + off[k]][0]; };
-        axis_terms<0>(nbp, s, c, uc, Tc, t);
+        auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[ty][sx + off[k]]; };
+        axis_terms<0>(nbp, sf, c, uc, t);
       }
       {
-        const T s[4] = {sm.s1buf[sy - 2][tx], sm.s1buf[sy - 1][tx], sm.s1buf[sy + 1][tx], sm.s1buf[sy + 2][tx]};
         const int off[4] = {-2, -1, 1, 2};
         auto nbp = [&](int k) { return &C[sy + off[k]][sx][0]; };
-        axis_terms<1>(nbp, s, c, uc, Tc, t);
+        auto sf = [&](int k, const T(&)[NV]) { return sm.s1buf[sy + off[k]][tx]; };
+        axis_terms<1>(nbp, sf, c, uc, t);
       }
       {
         const int zs[4] = {sl[0], sl[1], sl[3], sl[4]};
-        T s[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s[k] = sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx];
         auto nbp = [&](int k) { return &sm.ring[zs[k]][sy][sx][0]; };
-        axis_terms<2>(nbp, s, c, uc, Tc, t);
+        auto sf = [&](int k, const T(&)[NV]) { return sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx]; };
+        axis_terms<2>(nbp, sf, c, uc, t);
       }
 
       // assemble Eqs. 1-3
+      const T e0sum = c.e0[0] + c.e0[1] + c.e0[2];  // centre coefficient of the Laplacian
       const T div = t.g[0][0] + t.g[1][1] + t.g[2][2];
       const T rho = T(1) + rho_p;
       T R[5];
@@ -389,15 +424,17 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
       T uvisc = T(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const T visc = t.lap[i] + t.G[i] * T(1.0 / 3.0);  // Laplacian + G - (2/3) G
+        const T lap = fma(e0sum, uc[i], t.lap[i]);
+        const T visc = lap + t.G[i] * T(1.0 / 3.0);  // Laplacian + G - (2/3) G
         uvisc += uc[i] * visc;
-        R[1 + i] = T(-0.5) * (t.rm[i] + mc[i] * div) + t.rmx[i] + c.inv_re * visc;
+        R[1 + i] = T(-0.5) * (t.rM[i] + mc[i] * div) + c.inv_re * visc;
       }
       // viscous dissipation du_i/dx_j (du_i/dx_j + du_j/dx_i - 2/3 div delta_ij)
       const T a01 = t.g[0][1] + t.g[1][0], a02 = t.g[0][2] + t.g[2][0], a12 = t.g[1][2] + t.g[2][1];
       const T diss = T(2) * (t.g[0][0] * t.g[0][0] + t.g[1][1] * t.g[1][1] + t.g[2][2] * t.g[2][2]) + a01 * a01 +
                      a02 * a02 + a12 * a12 - T(2.0 / 3.0) * div * div;
-      R[4] = -t.rE1 - T(0.5) * (t.rE2 + Ec * div) - c.H0 * div + c.inv_re * (uvisc + diss) + c.kappa * t.lapT;
+      const T lapT = fma(e0sum, Tc, t.lapT);
+      R[4] = T(-0.5) * (t.rE + Ec * div) - c.H0 * div + c.inv_re * (uvisc + diss) + c.kappa * lapT;
 
       if (valid_xy) {
         if (RHS_ONLY) {
@@ -433,29 +470,46 @@ __global__ void __launch_bounds__(TX* TY, (sizeof(T) == 8 ? 1 : 2))
     }
     __syncthreads();
   }
+}
 
-  if (WITH_KE) {
-    // fixed-order block reduction: warp shuffles, then warp 0 over warps
+// Fixed-order block reduction of (ke, ens) into out[0..1]: warp shuffles,
+// then thread 0 over the warps.
+template <int NT>
+__device__ __forceinline__ void block_reduce_pair(double (&red)[2][32], double ke, double ens, double* out) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ke_acc += __shfl_down_sync(0xffffffffu, ke_acc, o);
-      ens_acc += __shfl_down_sync(0xffffffffu, ens_acc, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    ke += __shfl_down_sync(0xffffffffu, ke, o);
+    ens += __shfl_down_sync(0xffffffffu, ens, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ke;
+    red[1][threadIdx.x >> 5] = ens;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double k = 0.0, e = 0.0;
+    for (int w = 0; w < NT / 32; ++w) {
+      k += red[0][w];
+      e += red[1][w];
     }
-    if ((tid & 31) == 0) {
-      sm.red[0][tid >> 5] = ke_acc;
-      sm.red[1][tid >> 5] = ens_acc;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double k = 0.0, e = 0.0;
-      for (int w = 0; w < NT / 32; ++w) {
-        k += sm.red[0][w];
-        e += sm.red[1][w];
-      }
-      const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-      a.ke_partials[2 * b] = k;
-      a.ke_partials[2 * b + 1] = e;
-    }
+    out[0] = k;
+    out[1] = e;
+  }
+  __syncthreads();
+}
+
+// Single grid: one CTA per (tile, z chunk).
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
+__global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
+    fused_stage_kernel(const StageArgs a, const Coef<T> c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FusedSmem<T, TY>& sm = *reinterpret_cast<FusedSmem<T, TY>*>(smem_raw);
+  double ke = 0.0, ens = 0.0;
+  const int zbeg = blockIdx.z * a.zc;
+  fused_march<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE>(a, c, blockIdx.x, blockIdx.y, zbeg, zbeg + a.zc, sm, ke, ens);
+  if (WITH_KE) {
+    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    block_reduce_pair<TX * TY>(sm.red, ke, ens, a.ke_partials + 2 * b);
   }
 }
 

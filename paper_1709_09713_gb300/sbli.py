@@ -46,7 +46,22 @@ SIGNATURES = {
     "sbli_kinetic_energy": (_c_int, [_vp, _DP, _DP]),
     "sbli_kinetic_energy_async": (_c_int, [_vp, _vp]),
     "sbli_kinetic_energy_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _vp]),
+    "sbli_get_config": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "sbli_set_config": (_c_int, [_vp, _c_int, _c_int]),
+    "sbli_autotune": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                               ctypes.POINTER(ctypes.c_float)]),
     "sbli_stage_count": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sbli_batch_workspace_bytes": (_c_int, [_c_int, _vp, _c_int, ctypes.POINTER(_c_size_t)]),
+    "sbli_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _vp, _vp, _c_int, _vp, _c_size_t, _vp]),
+    "sbli_batch_destroy": (_c_int, [_vp]),
+    "sbli_batch_count": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "sbli_batch_work_items": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sbli_batch_init_tgv": (_c_int, [_vp, _vp]),
+    "sbli_batch_set_state": (_c_int, [_vp, _c_int, _vp, _c_int]),
+    "sbli_batch_get_state": (_c_int, [_vp, _c_int, _vp, _c_int]),
+    "sbli_batch_step_n": (_c_int, [_vp, _c_int, _c_double]),
+    "sbli_batch_step_n_history": (_c_int, [_vp, _c_int, _c_double, _vp]),
+    "sbli_batch_kinetic_energy": (_c_int, [_vp, _vp, _vp]),
     "sbli_last_error": (ctypes.c_char_p, []),
 }
 
@@ -157,10 +172,161 @@ def sbli_kinetic_energy_noalloc(q_ptr: int, n0: int, n1: int, n2: int, L: float,
     _check(lib().sbli_kinetic_energy_noalloc(_vp(q_ptr), n0, n1, n2, float(L), _vp(out_ptr), _vp(stream)))
 
 
+def sbli_get_config(h: int) -> tuple[int, int]:
+    ty, zc = _c_int(), _c_int()
+    _check(lib().sbli_get_config(_vp(h), ctypes.byref(ty), ctypes.byref(zc)))
+    return ty.value, zc.value
+
+
+def sbli_set_config(h: int, tile_y: int, planes_per_cta: int) -> None:
+    _check(lib().sbli_set_config(_vp(h), int(tile_y), int(planes_per_cta)))
+
+
+def sbli_autotune(h: int, reps: int = 3) -> tuple[int, int, float]:
+    ty, zc, ms = _c_int(), _c_int(), ctypes.c_float()
+    _check(lib().sbli_autotune(_vp(h), int(reps), ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ms)))
+    return ty.value, zc.value, ms.value
+
+
 def sbli_stage_count(h: int) -> int:
     v = ctypes.c_longlong()
     _check(lib().sbli_stage_count(_vp(h), ctypes.byref(v)))
     return v.value
+
+
+def _ints(vals):
+    return (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+
+
+def _doubles(vals):
+    return (ctypes.c_double * len(vals))(*[float(v) for v in vals])
+
+
+def sbli_batch_workspace_bytes(sizes, precision: int) -> int:
+    flat = [v for n in sizes for v in n]
+    out = _c_size_t()
+    _check(lib().sbli_batch_workspace_bytes(len(sizes), ctypes.cast(_ints(flat), _vp), precision, ctypes.byref(out)))
+    return out.value
+
+
+def sbli_batch_create(sizes, prms, precision: int, workspace_ptr: int, workspace_bytes: int, stream: int) -> int:
+    flat = [v for n in sizes for v in n]
+    parr = (Params * len(prms))(*prms)
+    h = _vp()
+    _check(lib().sbli_batch_create(ctypes.byref(h), len(sizes), ctypes.cast(_ints(flat), _vp), ctypes.cast(parr, _vp),
+                                   precision, _vp(workspace_ptr), workspace_bytes, _vp(stream)))
+    return h.value
+
+
+def sbli_batch_destroy(h: int) -> None:
+    _check(lib().sbli_batch_destroy(_vp(h)))
+
+
+def sbli_batch_count(h: int) -> int:
+    v = _c_int()
+    _check(lib().sbli_batch_count(_vp(h), ctypes.byref(v)))
+    return v.value
+
+
+def sbli_batch_work_items(h: int) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().sbli_batch_work_items(_vp(h), ctypes.byref(v)))
+    return v.value
+
+
+def sbli_batch_init_tgv(h: int, amplitudes) -> None:
+    _check(lib().sbli_batch_init_tgv(_vp(h), ctypes.cast(_doubles(amplitudes), _vp)))
+
+
+def sbli_batch_set_state(h: int, member: int, q_ptr: int, q_is_host: bool) -> None:
+    _check(lib().sbli_batch_set_state(_vp(h), member, _vp(q_ptr), int(bool(q_is_host))))
+
+
+def sbli_batch_get_state(h: int, member: int, q_ptr: int, q_is_host: bool) -> None:
+    _check(lib().sbli_batch_get_state(_vp(h), member, _vp(q_ptr), int(bool(q_is_host))))
+
+
+def sbli_batch_step_n(h: int, nsteps: int, dt: float) -> None:
+    _check(lib().sbli_batch_step_n(_vp(h), int(nsteps), float(dt)))
+
+
+def sbli_batch_step_n_history(h: int, nsteps: int, dt: float, hist_ptr: int) -> None:
+    _check(lib().sbli_batch_step_n_history(_vp(h), int(nsteps), float(dt), _vp(hist_ptr)))
+
+
+def sbli_batch_kinetic_energy(h: int, count: int):
+    ke = (ctypes.c_double * count)()
+    ens = (ctypes.c_double * count)()
+    _check(lib().sbli_batch_kinetic_energy(_vp(h), ctypes.cast(ke, _vp), ctypes.cast(ens, _vp)))
+    return list(ke), list(ens)
+
+
+class Batch:
+    """An ensemble of grids advanced together (workspace tensor + handle)."""
+
+    def __init__(self, sizes, precision=SBLI_FP32, Re=None, Mach=None, Pr=0.71, gamma=1.4, L=1.0, stream=None):
+        import torch
+
+        self.sizes = [(n, n, n) if isinstance(n, int) else tuple(int(v) for v in n) for n in sizes]
+        count = len(self.sizes)
+        Re = Re if Re is not None else [1600.0] * count
+        Mach = Mach if Mach is not None else [0.1] * count
+        self.prms = [params(Re[i], Mach[i], Pr, gamma, L) for i in range(count)]
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.bytes = sbli_batch_workspace_bytes(self.sizes, precision)
+        self.workspace = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.handle = sbli_batch_create(self.sizes, self.prms, precision, aligned, self.bytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sbli_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def shape(self, m):
+        n = self.sizes[m]
+        return (5, n[2], n[1], n[0])
+
+    def init_tgv(self, amplitudes=None):
+        sbli_batch_init_tgv(self.handle, amplitudes if amplitudes is not None else [1.0] * len(self))
+
+    def set_state(self, m, q):
+        sbli_batch_set_state(self.handle, m, q.data_ptr(), not q.is_cuda)
+
+    def get_state(self, m, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.shape(m), dtype=torch.float64, device=self.device)
+        sbli_batch_get_state(self.handle, m, out.data_ptr(), not out.is_cuda)
+        return out
+
+    def step_n(self, nsteps, dt):
+        sbli_batch_step_n(self.handle, nsteps, dt)
+
+    def step_n_history(self, nsteps, dt):
+        import torch
+
+        hist = torch.empty((max(nsteps, 1), len(self), 2), dtype=torch.float64, device=self.device)
+        sbli_batch_step_n_history(self.handle, nsteps, dt, hist.data_ptr())
+        return hist[:nsteps]
+
+    def kinetic_energy(self):
+        return sbli_batch_kinetic_energy(self.handle, len(self))
+
+    def work_items(self):
+        return sbli_batch_work_items(self.handle)
 
 
 def sbli_last_error() -> str:
@@ -257,6 +423,15 @@ class Grid:
 
     def kinetic_energy(self):
         return sbli_kinetic_energy(self.handle)
+
+    def config(self):
+        return sbli_get_config(self.handle)
+
+    def set_config(self, tile_y, planes_per_cta):
+        sbli_set_config(self.handle, tile_y, planes_per_cta)
+
+    def autotune(self, reps=3):
+        return sbli_autotune(self.handle, reps)
 
     def stage_count(self):
         return sbli_stage_count(self.handle)

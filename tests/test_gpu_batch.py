@@ -1,0 +1,93 @@
+"""Batched ensembles (one persistent launch per stage over all members,
+graph-captured step loops): every member's result is bitwise the result of
+the same problem run alone, and the alone result is tied to the oracle by
+test_gpu_parity."""
+import numpy as np
+import pytest
+
+from paper_1709_09713_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_09713_gb300 import build
+
+    build.build()
+    from paper_1709_09713_gb300 import sbli
+
+    sbli.lib()
+    return sbli
+
+
+SIZES = [(32, 32, 32), (48, 48, 48), (20, 16, 12), (64, 40, 24), (5, 6, 7)]
+RE = [1600.0, 300.0, 100.0, 900.0, 50.0]
+MACH = [0.1, 0.25, 0.4, 0.15, 0.3]
+AMP = [1.0, 0.95, 1.08, 0.9, 1.02]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_members_equal_single_grids_bitwise(S, precision):
+    dt, steps = 1e-3, 7  # one captured 6-step graph plus one direct step
+    b = S.Batch(SIZES, precision, Re=RE, Mach=MACH)
+    b.init_tgv(AMP)
+    b.step_n(steps, dt)
+    for m, n in enumerate(SIZES):
+        g = S.Grid(n, precision, S.SBLI_FUSED, Re=RE[m], Mach=MACH[m])
+        g.set_config(8, min(32, n[2]))
+        g.init_tgv(AMP[m])
+        g.step_n(steps, dt)
+        assert torch.equal(b.get_state(m), g.get_state()), m
+
+
+def test_batch_matches_oracle_fp64(S, orc):
+    dt, steps = 1e-3, 3
+    b = S.Batch(SIZES[:3], 0, Re=RE[:3], Mach=MACH[:3])
+    b.init_tgv(AMP[:3])
+    b.step_n(steps, dt)
+    for m, n in enumerate(SIZES[:3]):
+        p = orc.params(n, Re=RE[m], Mach=MACH[m])
+        want = orc.step(p, orc.init_tgv(p, AMP[m]), dt, steps)
+        got = b.get_state(m).cpu().numpy()
+        mom = np.max(np.abs(want[1:4]))
+        for f in range(5):
+            den = mom if 1 <= f <= 3 else np.max(np.abs(want[f]))
+            assert np.max(np.abs(got[f] - want[f])) / den <= 1e-12, (m, f)
+
+
+def test_batch_history_and_set_state(S):
+    dt, steps = 1e-3, 3
+    sizes = SIZES[:4]
+    b = S.Batch(sizes, 1, Re=RE[:4], Mach=MACH[:4])
+    rng = np.random.default_rng(5)
+    for m, n in enumerate(sizes):
+        e0 = 1.0 / (1.4 * 0.4 * MACH[m] ** 2) + 0.5
+        q = workloads.smooth_state(n, 40 + m, offsets=(1.0, 0, 0, 0, e0), amplitudes=(0.05, 0.3, 0.3, 0.3, 0.3))
+        b.set_state(m, torch.from_numpy(q).cuda())
+    hist = b.step_n_history(steps, dt).cpu().numpy()
+    ke, ens = b.kinetic_energy()
+    for m, n in enumerate(sizes):
+        g = S.Grid(n, 1, S.SBLI_FUSED, Re=RE[m], Mach=MACH[m])
+        e0 = 1.0 / (1.4 * 0.4 * MACH[m] ** 2) + 0.5
+        q = workloads.smooth_state(n, 40 + m, offsets=(1.0, 0, 0, 0, e0), amplitudes=(0.05, 0.3, 0.3, 0.3, 0.3))
+        g.set_state(torch.from_numpy(q).cuda())
+        h = g.step_n_history(steps, dt).cpu().numpy()
+        assert np.allclose(hist[:, m, :], h, rtol=1e-12, atol=0)
+        k1, e1 = g.kinetic_energy()
+        assert ke[m] == pytest.approx(k1, rel=1e-13) and ens[m] == pytest.approx(e1, rel=1e-13)
+        assert torch.equal(b.get_state(m), g.get_state())
+
+
+def test_batch_ensemble_draws_build(S):
+    members = workloads.ensemble(8, seed=1709, sizes=(32, 48))
+    b = S.Batch([mm.n for mm in members], 1, Re=[mm.Re for mm in members], Mach=[mm.Mach for mm in members])
+    b.init_tgv([mm.amplitude for mm in members])
+    b.step_n(2, 1e-3)
+    ke, _ = b.kinetic_energy()
+    assert all(np.isfinite(ke)) and all(k > 0 for k in ke)
+    with pytest.raises(S.SbliError):
+        S.sbli_batch_workspace_bytes([(4, 8, 8)], 1)

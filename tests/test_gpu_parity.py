@@ -227,3 +227,52 @@ def test_error_paths_fault_nothing(S):
         S.sbli_create_grid(8, 8, 8, 0, 0, S.params(), (host.data_ptr() + 255) // 256 * 256, 1 << 19, 0)
     assert e.value.code in (S.SBLI_EINVAL, S.SBLI_ENOMEM)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("precision,configs", [(1, [(8, 4), (8, 13), (16, 7), (16, 40)]), (0, [(8, 4), (8, 9), (8, 40)])])
+def test_launch_configs_are_bitwise_identical(S, precision, configs):
+    """Tile height and planes per CTA change only the work decomposition:
+    every point's arithmetic is the same, so the state is bitwise equal."""
+    n, dt = (64, 48, 40), 1e-3
+    q = to_dev(random_state(n, 23))
+    ref = None
+    for ty, zc in configs:
+        g = S.Grid(n, precision, S.SBLI_FUSED)
+        g.set_config(ty, zc)
+        assert g.config() == (ty, min(zc, n[2]))
+        g.set_state(q)
+        g.step_n(2, dt)
+        out = g.get_state()
+        if ref is None:
+            ref = out
+        else:
+            assert torch.equal(out, ref), (ty, zc)
+
+
+def test_autotune_keeps_state_and_picks_a_valid_config(S):
+    n = (64, 64, 64)
+    g = S.Grid(n, S.SBLI_FP32, S.SBLI_FUSED)
+    g.init_tgv()
+    before = g.get_state()
+    ty, zc, ms = g.autotune(reps=2)
+    assert ty in (8, 16) and 4 <= zc <= n[2] and ms > 0
+    assert torch.equal(g.get_state(), before)
+    assert g.config() == (ty, zc)
+    g.step_n(1, 1e-3)
+    with pytest.raises(S.SbliError):
+        g.set_config(12, 8)
+
+
+def test_fp32_kinetic_energy_history_512_subsample_bound(S, orc):
+    """FP32 path against the binary64 GPU path at a larger grid (64^3, 20
+    steps): fields within 1e-5, KE history within 1e-6."""
+    n, dt, steps = 64, 1e-3, 20
+    a = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
+    b = S.Grid(n, S.SBLI_FP32, S.SBLI_FUSED)
+    a.init_tgv()
+    b.init_tgv()
+    ha = a.step_n_history(steps, dt).cpu().numpy()
+    hb = b.step_n_history(steps, dt).cpu().numpy()
+    assert np.max(np.abs(hb[:, 0] - ha[:, 0]) / ha[:, 0]) <= 1e-6
+    errs = rel_fields(b.get_state().cpu().numpy(), a.get_state().cpu().numpy())
+    assert max(errs) <= 1e-5, errs
