@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--no-legs", action="store_true", help="skip the FP32 512^3 and store-all legs")
     ap.add_argument("--leg-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-nmax", type=int, default=128)
+    ap.add_argument("--serve-steps-hi", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
@@ -240,6 +243,52 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709):
             "stage_ms": ms / (3 * steps), "launches_per_stage": 1}
 
 
+def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, arena_gb=200.0):
+    """Poisson arrivals of TGV solve requests (grid edge log-uniform, step
+    count uniform, FP64/FP32 flag 50/50) replayed in wall-clock time against
+    the continuous-batching server; latency = completion - arrival."""
+    import torch
+
+    from paper_1709_09713_gb300 import workloads
+
+    trace = workloads.request_trace(count, seed=seed, rate_hz=rate_hz, nmin=nmin, nmax=nmax, steps_lo=steps_lo,
+                                    steps_hi=steps_hi)
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(arena_gb * 2**30, free * 0.8))
+    srv = S.Server(arena, max_slots=64, backfill=True)
+    t0 = time.perf_counter()
+    nxt, res, arrival = 0, {}, {}
+    while len(res) < count:
+        now = time.perf_counter() - t0
+        while nxt < count and trace[nxt].arrival_s <= now:
+            q = trace[nxt]
+            rid = srv.submit(S.request(q.n, q.precision, q.steps, 1e-3, Re=q.Re, Mach=q.Mach, amplitude=q.amplitude))
+            arrival[rid] = q.arrival_s
+            nxt += 1
+        st = srv.stats()
+        if st.active == 0 and st.pending == 0 and nxt < count:
+            time.sleep(max(0.0, min(0.01, trace[nxt].arrival_s - now)))
+            continue
+        srv.tick()
+        for r in srv.poll():
+            res[r.id] = (r, time.perf_counter() - t0)
+    wall = time.perf_counter() - t0
+    srv.close()
+    del srv
+    torch.cuda.empty_cache()
+    lat = sorted(done_t - arrival[rid] for rid, (r, done_t) in res.items())
+    work = sum(3.0 * r.points * r.steps for r, _ in res.values())
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+
+    return {"workload": f"serving: {count} Poisson requests at {rate_hz} req/s, N log-uniform [{nmin},{nmax}], "
+                        f"steps U{{{steps_lo}..{steps_hi}}}, fp64/fp32 50/50, dt 1e-3",
+            "value": work / wall, "unit": "pt-stage/s", "requests": count, "wall_s": wall,
+            "p50_latency_s": pct(50), "p99_latency_s": pct(99), "max_latency_s": lat[-1],
+            "offered_pt_stage_per_s": sum(3.0 * q.n**3 * q.steps for q in trace) / max(trace[-1].arrival_s, 1e-9)}
+
+
 def leg(S, n, precision, variant, steps, warmup, dt, ws):
     """Throughput of one extra configuration (no e2e, no clocks)."""
     import torch
@@ -383,7 +432,8 @@ def run_ours(args):
     if not args.no_legs:
         line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws),
                         leg(S, 256, "fp64", "store_all", max(3, args.leg_steps // 4), 1, dt, ws),
-                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws)]
+                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws),
+                        serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_n, args.cpu_sample_steps, dt)
     if rank == 0:

@@ -210,6 +210,63 @@ SBLI_API int sbli_batch_step_n_history(sbli_batch* b, int nsteps, double dt, dou
  * enstrophy[count].  Synchronises the batch's stream. */
 SBLI_API int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstrophy);
 
+/* ---------------------------------------------------------------------
+ * Serving: a continuous-batching request loop.  Requests wait in arrival
+ * order and are admitted when one of max_slots slots and a block of the
+ * caller's device arena are free (first fit; with backfill != 0 a later
+ * request that fits may pass one that does not).  Admitted requests keep
+ * their state resident; each sbli_server_tick advances every active request
+ * by one time step (binary64 and binary32 requests as two persistent
+ * multi-member launches per stage on the two given streams, which overlap on
+ * the device), then retires the finished ones: binary64 kinetic energy and
+ * enstrophy of the final state, optional copy of the state to `result`, and
+ * release of the block.  A request's result equals the same problem run
+ * alone as a single grid with tile height 8, bitwise.
+ * --------------------------------------------------------------------- */
+typedef struct sbli_server sbli_server;
+
+typedef struct {
+  int n0, n1, n2;      /* grid */
+  int precision;       /* SBLI_FP64 or SBLI_FP32 */
+  int steps;           /* time steps to run (>= 0) */
+  double dt;           /* time step (> 0) */
+  sbli_params params;  /* Re, M, Pr, gamma, L */
+  double amplitude;    /* Taylor-Green velocity amplitude of the initial field */
+  double* result;      /* final plain state (5*P binary64) is copied here, or NULL */
+  int result_is_host;  /* result is host memory */
+} sbli_request;
+
+typedef struct {
+  long long id;        /* as returned by sbli_server_submit */
+  double ke, enstrophy;  /* volume averages of the final state (binary64) */
+  double t_submit, t_admit, t_done;  /* seconds since server creation */
+  int steps, precision;
+  long long points;
+} sbli_result;
+
+typedef struct {
+  int pending, active, completed_unpolled;
+  size_t free_bytes, largest_free_block, arena_bytes;
+  long long ticks;
+  double now;          /* seconds since server creation */
+} sbli_server_status;
+
+/* arena: caller-owned device memory (256-byte aligned) the server carves into
+ * per-request blocks; it stays owned by the caller. */
+SBLI_API int sbli_server_create(sbli_server** out, void* arena, size_t arena_bytes, int max_slots, int backfill,
+                                void* stream_fp64, void* stream_fp32);
+SBLI_API int sbli_server_destroy(sbli_server* s);
+/* Device bytes a request occupies while active. */
+SBLI_API int sbli_server_request_bytes(const sbli_request* r, size_t* bytes);
+/* Queue a request (copied); SBLI_ENOMEM if it can never fit the arena. */
+SBLI_API int sbli_server_submit(sbli_server* s, const sbli_request* r, long long* id);
+/* Admit, advance every active request one step, retire finished ones.
+ * Synchronises both streams; *completed = requests retired by this tick. */
+SBLI_API int sbli_server_tick(sbli_server* s, int* completed);
+/* Move up to max retired requests' results into out; *n = how many. */
+SBLI_API int sbli_server_poll(sbli_server* s, sbli_result* out, int max, int* n);
+SBLI_API int sbli_server_stats(const sbli_server* s, sbli_server_status* status);
+
 /* Number of stages completed since creation or the last set_state/init. */
 SBLI_API int sbli_stage_count(const sbli_grid* g, long long* stages);
 

@@ -16,23 +16,10 @@
 #include <algorithm>
 #include <vector>
 
+#include "batch_kernel.cuh"
 #include "fused_stage.cuh"
 
 namespace sbli {
-
-constexpr int BATCH_MAX_MEMBERS = 64;  // members per launch (parameter space bound)
-
-template <typename T>
-struct BatchParams {
-  int count;                                  // members in this launch
-  long long total_items;                      // sum of the members' items
-  long long item_begin[BATCH_MAX_MEMBERS + 1];
-  int tiles_x[BATCH_MAX_MEMBERS];
-  int tiles_y[BATCH_MAX_MEMBERS];
-  StageArgs a[BATCH_MAX_MEMBERS];             // geometry, zc, stage pointers, a_k dt, b_k dt
-  Coef<T> c[BATCH_MAX_MEMBERS];
-  double* ke_items;                           // per-item (ke, ens) partials, or nullptr
-};
 
 template <typename T, typename TIN, typename TOUT, int TY, bool WITH_KE>
 __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
@@ -78,6 +65,54 @@ __global__ void __launch_bounds__(256) batch_ke_finalize(const double* __restric
   }
 }
 
+// ---- launchers (declared in batch_kernel.cuh)
+template <>
+cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(FusedSmem<float, 8>);
+  static bool cfg = false;
+  if (!cfg) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, float, float, 8, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    cfg = true;
+  }
+  if (in64) {
+    if (p.ke_items) batch_stage_kernel<float, double, float, 8, true><<<grid, TX * 8, smem, s>>>(p);
+    else batch_stage_kernel<float, double, float, 8, false><<<grid, TX * 8, smem, s>>>(p);
+  } else {
+    batch_stage_kernel<float, float, float, 8, false><<<grid, TX * 8, smem, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(FusedSmem<double, 8>);
+  static bool cfg = false;
+  if (!cfg) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<double, double, double, 8, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<double, double, double, 8, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    cfg = true;
+  }
+  if (p.ke_items) batch_stage_kernel<double, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
+  else batch_stage_kernel<double, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_batch_ke_finalize(const double* items, const long long* begin, const double* inv_p, double* out,
+                                     int count, cudaStream_t s) {
+  batch_ke_finalize<<<count, 256, 0, s>>>(items, begin, inv_p, out);
+  return cudaGetLastError();
+}
+
 }  // namespace sbli
 
 using namespace sbli;
@@ -120,11 +155,6 @@ struct BatchLayout {
   long long total_items;
 };
 
-int batch_zc(int n2) { return std::min(n2, 32); }
-
-long long member_items(const int n[3], int ty) {
-  return (long long)((n[0] + TX - 1) / TX) * ((n[1] + ty - 1) / ty) * ((n[2] + batch_zc(n[2]) - 1) / batch_zc(n[2]));
-}
 
 BatchLayout batch_layout(int count, const int* n, int precision) {
   BatchLayout L;
@@ -139,7 +169,7 @@ BatchLayout batch_layout(int count, const int* n, int precision) {
     M.off32 = o32;
     o64 += balign((size_t)M.P * 5 * sizeof(double));
     o32 += balign((size_t)M.P * 5 * sizeof(float));
-    L.total_items += member_items(M.n, 8);
+    L.total_items += member_items(M.n);
   }
   L.reg64 = o64;
   L.reg32 = precision == SBLI_FP64 ? 0 : o32;
@@ -212,49 +242,6 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
 }
 
 template <typename T>
-cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStream_t s);
-
-template <>
-cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(FusedSmem<float, 8>);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, float, float, 8, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    cfg = true;
-  }
-  if (in64) {
-    if (p.ke_items) batch_stage_kernel<float, double, float, 8, true><<<grid, TX * 8, smem, s>>>(p);
-    else batch_stage_kernel<float, double, float, 8, false><<<grid, TX * 8, smem, s>>>(p);
-  } else {
-    batch_stage_kernel<float, float, float, 8, false><<<grid, TX * 8, smem, s>>>(p);
-  }
-  return cudaGetLastError();
-}
-
-template <>
-cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(FusedSmem<double, 8>);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<double, double, double, 8, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<double, double, double, 8, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    cfg = true;
-  }
-  if (p.ke_items) batch_stage_kernel<double, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
-  else batch_stage_kernel<double, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t enqueue_batch_stage_t(sbli_batch* b, int k, int state, double dt, double* ke_items, cudaStream_t s) {
   BatchParams<T> p;
   memset(&p, 0, sizeof p);
@@ -267,7 +254,7 @@ cudaError_t enqueue_batch_stage_t(sbli_batch* b, int k, int state, double dt, do
     p.item_begin[m] = acc;
     p.tiles_x[m] = (M.n[0] + TX - 1) / TX;
     p.tiles_y[m] = (M.n[1] + 7) / 8;
-    acc += member_items(M.n, 8);
+    acc += member_items(M.n);
     p.a[m] = member_stage(b, m, k, state, dt, &in64);
     p.c[m] = make_coef<T>(M.n, b->params[m]);
   }
@@ -393,7 +380,7 @@ int sbli_batch_create(sbli_batch** out, int count, const int* n, const sbli_para
   for (int m = 0; m < count; ++m) {
     inv[m] = 1.0 / (double)b->L.m[m].P;
     beg[m] = acc;
-    acc += member_items(b->L.m[m].n, 8);
+    acc += member_items(b->L.m[m].n);
   }
   beg[count] = acc;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
@@ -493,9 +480,9 @@ int sbli_batch_step_n_history(sbli_batch* b, int nsteps, double dt, double* ke_h
   if (!(dt > 0) || !isfinite(dt)) return bfail(SBLI_EINVAL, "dt must be finite and > 0");
   for (int s = 0; s < nsteps; ++s) {
     SBLI_BTRY(enqueue_batch_stage(b, 0, b->state, dt, b->ke_items, b->stream), "batch stage");
-    batch_ke_finalize<<<b->count, 256, 0, b->stream>>>(b->ke_items, b->begin, b->inv_p,
-                                                        ke_hist_dev + (size_t)2 * b->count * s);
-    SBLI_BTRY(cudaGetLastError(), "ke finalize");
+    SBLI_BTRY(launch_batch_ke_finalize(b->ke_items, b->begin, b->inv_p, ke_hist_dev + (size_t)2 * b->count * s,
+                                       b->count, b->stream),
+              "ke finalize");
     for (int k = 1; k < 3; ++k) SBLI_BTRY(enqueue_batch_stage(b, k, b->state, dt, nullptr, b->stream), "batch stage");
     b->state = batch_next_state(b, b->state);
     b->steps_done++;

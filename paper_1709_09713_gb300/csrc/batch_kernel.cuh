@@ -1,0 +1,38 @@
+// batch_kernel.cuh -- the multi-member stage launch shared by ensembles
+// (batch.cu) and the serving loop (server.cu).
+#pragma once
+
+#include "sbli_internal.cuh"
+
+namespace sbli {
+
+constexpr int BATCH_MAX_MEMBERS = 64;  // members per launch (parameter space bound)
+
+template <typename T>
+struct BatchParams {
+  int count;                                  // members in this launch
+  long long total_items;                      // sum of the members' items
+  long long item_begin[BATCH_MAX_MEMBERS + 1];
+  int tiles_x[BATCH_MAX_MEMBERS];
+  int tiles_y[BATCH_MAX_MEMBERS];
+  StageArgs a[BATCH_MAX_MEMBERS];             // geometry, zc, stage pointers, a_k dt, b_k dt
+  Coef<T> c[BATCH_MAX_MEMBERS];
+  double* ke_items;                           // per-item (ke, ens) partials, or nullptr
+};
+
+// One persistent launch of stage work for p.count members (grid = CTAs).
+// in64: the members' stage inputs are binary64 (binary32 path, stage 0).
+template <typename T>
+cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStream_t s);
+
+// Work items (z chunk x 32 x 8 tile) of one member and its planes per item.
+inline int batch_zc(int n2) { return n2 < 32 ? n2 : 32; }
+inline long long member_items(const int n[3]) {
+  return (long long)((n[0] + 31) / 32) * ((n[1] + 7) / 8) * ((n[2] + batch_zc(n[2]) - 1) / batch_zc(n[2]));
+}
+
+// Per member m: fixed-order sum of item partials [begin[m], begin[m+1]) times inv_p[m].
+cudaError_t launch_batch_ke_finalize(const double* items, const long long* begin, const double* inv_p, double* out,
+                                     int count, cudaStream_t s);
+
+}  // namespace sbli

@@ -29,6 +29,24 @@ class Params(ctypes.Structure):
     _fields_ = [("Re", _c_double), ("Mach", _c_double), ("Pr", _c_double), ("gamma", _c_double), ("L", _c_double)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("n0", _c_int), ("n1", _c_int), ("n2", _c_int), ("precision", _c_int), ("steps", _c_int),
+                ("dt", _c_double), ("params", Params), ("amplitude", _c_double), ("result", _vp),
+                ("result_is_host", _c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("ke", _c_double), ("enstrophy", _c_double), ("t_submit", _c_double),
+                ("t_admit", _c_double), ("t_done", _c_double), ("steps", _c_int), ("precision", _c_int),
+                ("points", ctypes.c_longlong)]
+
+
+class ServerStatus(ctypes.Structure):
+    _fields_ = [("pending", _c_int), ("active", _c_int), ("completed_unpolled", _c_int), ("free_bytes", _c_size_t),
+                ("largest_free_block", _c_size_t), ("arena_bytes", _c_size_t), ("ticks", ctypes.c_longlong),
+                ("now", _c_double)]
+
+
 SIGNATURES = {
     "sbli_abi_version": (_c_int, []),
     "sbli_workspace_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_c_size_t)]),
@@ -62,6 +80,13 @@ SIGNATURES = {
     "sbli_batch_step_n": (_c_int, [_vp, _c_int, _c_double]),
     "sbli_batch_step_n_history": (_c_int, [_vp, _c_int, _c_double, _vp]),
     "sbli_batch_kinetic_energy": (_c_int, [_vp, _vp, _vp]),
+    "sbli_server_create": (_c_int, [ctypes.POINTER(_vp), _vp, _c_size_t, _c_int, _c_int, _vp, _vp]),
+    "sbli_server_destroy": (_c_int, [_vp]),
+    "sbli_server_request_bytes": (_c_int, [ctypes.POINTER(Request), ctypes.POINTER(_c_size_t)]),
+    "sbli_server_submit": (_c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
+    "sbli_server_tick": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "sbli_server_poll": (_c_int, [_vp, ctypes.POINTER(Result), _c_int, ctypes.POINTER(_c_int)]),
+    "sbli_server_stats": (_c_int, [_vp, ctypes.POINTER(ServerStatus)]),
     "sbli_last_error": (ctypes.c_char_p, []),
 }
 
@@ -327,6 +352,101 @@ class Batch:
 
     def work_items(self):
         return sbli_batch_work_items(self.handle)
+
+
+def request(n, precision=SBLI_FP64, steps=10, dt=1e-3, Re=1600.0, Mach=0.1, Pr=0.71, gamma=1.4, L=1.0,
+            amplitude=1.0, result=None) -> Request:
+    """A solve request; ``result`` is an optional float64 tensor (5, n2, n1, n0)."""
+    n = (n, n, n) if isinstance(n, int) else tuple(int(v) for v in n)
+    r = Request()
+    r.n0, r.n1, r.n2 = n
+    r.precision, r.steps, r.dt = int(precision), int(steps), float(dt)
+    r.params = params(Re, Mach, Pr, gamma, L)
+    r.amplitude = float(amplitude)
+    r.result = _vp(result.data_ptr()) if result is not None else None
+    r.result_is_host = 0 if result is None or result.is_cuda else 1
+    return r
+
+
+def sbli_server_create(arena_ptr: int, arena_bytes: int, max_slots: int, backfill: bool, stream64: int,
+                       stream32: int) -> int:
+    h = _vp()
+    _check(lib().sbli_server_create(ctypes.byref(h), _vp(arena_ptr), arena_bytes, int(max_slots), int(bool(backfill)),
+                                    _vp(stream64), _vp(stream32)))
+    return h.value
+
+
+def sbli_server_destroy(h: int) -> None:
+    _check(lib().sbli_server_destroy(_vp(h)))
+
+
+def sbli_server_request_bytes(r: Request) -> int:
+    out = _c_size_t()
+    _check(lib().sbli_server_request_bytes(ctypes.byref(r), ctypes.byref(out)))
+    return out.value
+
+
+def sbli_server_submit(h: int, r: Request) -> int:
+    rid = ctypes.c_longlong()
+    _check(lib().sbli_server_submit(_vp(h), ctypes.byref(r), ctypes.byref(rid)))
+    return rid.value
+
+
+def sbli_server_tick(h: int) -> int:
+    n = _c_int()
+    _check(lib().sbli_server_tick(_vp(h), ctypes.byref(n)))
+    return n.value
+
+
+def sbli_server_poll(h: int, max_results: int = 256) -> list:
+    arr = (Result * max_results)()
+    n = _c_int()
+    _check(lib().sbli_server_poll(_vp(h), arr, max_results, ctypes.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def sbli_server_stats(h: int) -> ServerStatus:
+    st = ServerStatus()
+    _check(lib().sbli_server_stats(_vp(h), ctypes.byref(st)))
+    return st
+
+
+class Server:
+    """Continuous-batching request loop over a device arena tensor."""
+
+    def __init__(self, arena_bytes: int, max_slots: int = 64, backfill: bool = True):
+        import torch
+
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.s64 = torch.cuda.Stream()
+        self.s32 = torch.cuda.Stream()
+        self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.arena.data_ptr() + 255) // 256 * 256
+        self.handle = sbli_server_create(aligned, arena_bytes, max_slots, backfill, self.s64.cuda_stream,
+                                         self.s32.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sbli_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, r: Request) -> int:
+        return sbli_server_submit(self.handle, r)
+
+    def tick(self) -> int:
+        return sbli_server_tick(self.handle)
+
+    def poll(self) -> list:
+        return sbli_server_poll(self.handle)
+
+    def stats(self) -> ServerStatus:
+        return sbli_server_stats(self.handle)
 
 
 def sbli_last_error() -> str:
