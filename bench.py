@@ -170,6 +170,37 @@ def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def dist_max(x: float) -> float:
+    """Maximum of x over all ranks (identity without a process group).  Works
+    with nccl (CUDA tensor) and gloo (CPU tensor)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier() -> None:
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def weak_scaling_value(units_per_rank: float, seconds_this_rank: float) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time.  Returns (value, max_seconds)."""
+    import torch.distributed as dist
+
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = dist_max(seconds_this_rank)
+    return units_per_rank * ws / t, t
+
+
 def cpu_baseline(n: int, steps: int, dt: float):
     """The CPU oracle, unchanged, on an n^3 TGV for `steps` time steps on all host cores."""
     import oracle
@@ -189,8 +220,7 @@ def time_steps(S, g, stream, steps, dt, ws):
     """CUDA-event time of exactly `steps` steps on the grid's stream, max over ranks."""
     import torch
 
-    if ws > 1:
-        torch.distributed.barrier()
+    dist_barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -199,14 +229,8 @@ def time_steps(S, g, stream, steps, dt, ws):
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    dist_barrier()
+    return dist_max(e0.elapsed_time(e1))
 
 
 def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709):
@@ -364,8 +388,7 @@ def run_ours(args):
     g.get_state(q_host)
     e2e_t = []
     for _ in range(args.e2e_reps):
-        if ws > 1:
-            torch.distributed.barrier()
+        dist_barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         S.sbli_set_state(g.handle, q_host.data_ptr(), True)
@@ -373,11 +396,7 @@ def run_ours(args):
         S.sbli_get_state(g.handle, r_host.data_ptr(), True)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    t_e2e = min(e2e_t)
-    if ws > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = dist_max(min(e2e_t))
     state_bytes = 5 * P * 8
     g.close()
     del g

@@ -467,3 +467,16 @@ def test_point_and_grid_rhs_agree_bitwise(orc):
     for (i, j, k) in [(0, 0, 0), (5, 3, 2)]:
         qp, ap = orc.stage_point(p, 1, 1e-3, q, acc, i, j, k)
         assert np.array_equal(qp, qo[:, k, j, i]) and np.array_equal(ap, ao[:, k, j, i])
+
+
+def test_stage_chain_equals_rk_driver_bitwise(orc):
+    """The single-stage oracle used for per-stage GPU parity, chained over
+    stages 0, 1, 2, is the pinned three-stage driver (T6) bit for bit."""
+    n = (9, 8, 7)
+    p = orc.params(n, Re=200.0)
+    q0 = _state(orc, n, seed=31)
+    acc, q = q0.copy(), q0.copy()
+    for k in range(3):
+        q, acc = orc.stage(p, k, 2e-3, q, acc)
+    assert np.array_equal(acc, orc.step(p, q0, 2e-3, 1))
+    assert np.array_equal(q, acc)
