@@ -313,16 +313,21 @@ def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, aren
             "offered_pt_stage_per_s": sum(3.0 * q.n**3 * q.steps for q in trace) / max(trace[-1].arrival_s, 1e-9)}
 
 
-def leg(S, n, precision, variant, steps, warmup, dt, ws):
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2}
+
+
+def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False):
     """Throughput of one extra configuration (no e2e, no clocks)."""
     import torch
 
     stream = torch.cuda.Stream()
-    prec = S.SBLI_FP64 if precision == "fp64" else S.SBLI_FP32
+    prec = PRECISIONS[precision]
     var = S.SBLI_FUSED if variant == "fused" else S.SBLI_STORE_ALL
     g = S.Grid(n, prec, var, stream=stream)
     with torch.cuda.stream(stream):
         g.init_tgv(1.0)
+    cfg = list(g.autotune(3)[:2]) if tune else (list(g.config()) if var == S.SBLI_FUSED else None)
+    with torch.cuda.stream(stream):
         g.step_n(warmup, dt)
     ms = time_steps(S, g, stream, steps, dt, ws)
     g.close()
@@ -331,10 +336,11 @@ def leg(S, n, precision, variant, steps, warmup, dt, ws):
     P = n**3
     stage_ms = ms / (3 * steps)
     out = {"workload": f"TGV {n}^3 {precision} {variant}", "value": 3.0 * P * steps * ws / (ms / 1e3),
-           "unit": "pt-stage/s", "steps": steps, "stage_ms": stage_ms}
+           "unit": "pt-stage/s", "steps": steps, "stage_ms": stage_ms, "tile_y_planes": cfg,
+           "autotuned": bool(tune)}
     if variant == "fused":
         peaks, kind = measured_peaks()
-        ach = ALG_BYTES[precision] * P / (stage_ms / 1e3) / 1e9
+        ach = ALG_BYTES["fp64" if precision == "fp64" else "fp32"] * P / (stage_ms / 1e3) / 1e9
         out["hbm"] = {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                       "peak_source": kind}
     return out
@@ -449,7 +455,8 @@ def run_ours(args):
         line["energy"] = {"joules": joules, "j_per_pt_stage": joules / (3.0 * P * args.steps),
                           "source": "nvmlDeviceGetTotalEnergyConsumption delta over the timed region"}
     if not args.no_legs:
-        line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws),
+        line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
+                        leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
                         leg(S, 256, "fp64", "store_all", max(3, args.leg_steps // 4), 1, dt, ws),
                         ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi)]

@@ -25,7 +25,11 @@
  *    Precision SBLI_FP32: stage fields stored and the residual computed in
  *    binary32; the Runge-Kutta accumulator (the n+1 level of Fig. 1) and
  *    the state between steps are binary64; kinetic-energy and enstrophy sums
- *    are binary64.  Both store the state as deviations from the uniform
+ *    are binary64.  Precision SBLI_FP32_DF: as SBLI_FP32, but the accumulator
+ *    and the state between steps are double-float pairs (hi + lo, two
+ *    binary32, about 48 significant bits) updated with error-free binary32
+ *    additions, so no binary64 arithmetic runs in the stages (fused variant,
+ *    single grids only).  All store the state as deviations from the uniform
  *    reference state (rho = 1, u = 0, p = 1/(gamma M^2)); the
  *    get/set calls convert to and from the plain conserved variables.
  *  - Variant SBLI_FUSED evaluates every derivative on the fly and writes the
@@ -59,7 +63,7 @@ enum sbli_status {
   SBLI_EUNSUPPORTED = 5  /* precision/variant combination not provided */
 };
 
-enum sbli_precision { SBLI_FP64 = 0, SBLI_FP32 = 1 };
+enum sbli_precision { SBLI_FP64 = 0, SBLI_FP32 = 1, SBLI_FP32_DF = 2 };
 enum sbli_variant { SBLI_FUSED = 0, SBLI_STORE_ALL = 1 };
 
 /* Physical parameters (§2 Eqs. 1-5, §4): Re may be +INFINITY, which removes

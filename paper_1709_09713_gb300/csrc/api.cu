@@ -163,7 +163,7 @@ FusedConfig default_config(const Geom& g, int precision) {
 bool valid_config(int precision, int ty, int zc) {
   if (zc < 4) return false;
   if (precision == SBLI_FP64) return ty == 8;
-  return ty == 8 || ty == 16;
+  return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
 }
 
 // Pointers of stage k for the current rotation.
@@ -174,6 +174,8 @@ struct StagePtrs {
   double* acc_out;
   void* q_out;
   bool out64;
+  const float* dacc_in;  // double-float accumulator (SBLI_FP32_DF)
+  float* dacc_out;
 };
 
 StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
@@ -189,6 +191,19 @@ StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
       p.q_in = B; p.acc_in = A; p.acc_out = A; p.q_out = S;
     } else {
       p.q_in = S; p.acc_in = A; p.acc_out = A; p.q_out = nullptr;
+    }
+  } else if (g->precision == SBLI_FP32_DF) {
+    // double-float registers: the hi fields are the binary32 stage input
+    float* S = reinterpret_cast<float*>(g->reg64[state]);
+    float* A = reinterpret_cast<float*>(g->reg64[1 - state]);
+    p.out64 = false;
+    p.in64 = false;
+    if (k == 0) {
+      p.q_in = S; p.dacc_in = S; p.dacc_out = A; p.q_out = g->reg32[0];
+    } else if (k == 1) {
+      p.q_in = g->reg32[0]; p.dacc_in = A; p.dacc_out = A; p.q_out = g->reg32[1];
+    } else {
+      p.q_in = g->reg32[1]; p.dacc_in = A; p.dacc_out = A; p.q_out = nullptr;
     }
   } else {
     double* S = g->reg64[state];
@@ -224,7 +239,10 @@ cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_
     a.b_dt = b_dt;
     a.amb_dt = (RK_A[k] - RK_B[k]) * dt;
     a.ke_partials = ke_partials;
+    a.dacc_in = p.dacc_in;
+    a.dacc_out = p.dacc_out;
     if (g->precision == SBLI_FP64) return launch_fused_fp64(a, g->cd, g->cfg, false, s);
+    if (g->precision == SBLI_FP32_DF) return launch_fused_fp32df(a, g->cf, g->cfg, false, s);
     return launch_fused_fp32(a, g->cf, g->cfg, p.in64, false, s);
   }
   // store-all: residual into scratch, then the update kernel
@@ -297,8 +315,11 @@ const char* sbli_last_error(void) { return g_last_error.c_str(); }
 int sbli_workspace_bytes(int n0, int n1, int n2, int precision, int variant, size_t* bytes) {
   if (!bytes) return fail(SBLI_EINVAL, "bytes is null");
   if (!valid_sizes(n0, n1, n2)) return fail(SBLI_EINVAL, "grid %d x %d x %d: each edge must be >= 5 and n0*n1 < 2^31", n0, n1, n2);
-  if (precision != SBLI_FP64 && precision != SBLI_FP32) return fail(SBLI_EINVAL, "unknown precision %d", precision);
+  if (precision != SBLI_FP64 && precision != SBLI_FP32 && precision != SBLI_FP32_DF)
+    return fail(SBLI_EINVAL, "unknown precision %d", precision);
   if (variant != SBLI_FUSED && variant != SBLI_STORE_ALL) return fail(SBLI_EINVAL, "unknown variant %d", variant);
+  if (precision == SBLI_FP32_DF && variant != SBLI_FUSED)
+    return fail(SBLI_EUNSUPPORTED, "the double-float accumulator is provided for the fused variant only");
   *bytes = layout_for(n0, n1, n2, precision, variant).total;
   return SBLI_OK;
 }
@@ -374,6 +395,14 @@ int sbli_init_tgv(sbli_grid* g, double amplitude) {
   g->state = 0;
   g->next_stage = 0;
   g->stages_done = 0;
+  if (g->precision == SBLI_FP32_DF) {
+    // binary64 deviation field into the free register, then split into hi/lo
+    SBLI_TRY(launch_init_tgv(g->geom, g->params, amplitude, g->reg64[1], g->stream), "init_tgv launch");
+    const RefState zero{0.0, 0.0};
+    SBLI_TRY(launch_df_split(g->geom.P, zero, g->reg64[1], reinterpret_cast<float*>(g->reg64[0]), g->stream),
+             "df_split");
+    return SBLI_OK;
+  }
   SBLI_TRY(launch_init_tgv(g->geom, g->params, amplitude, g->reg64[0], g->stream), "init_tgv launch");
   return SBLI_OK;
 }
@@ -391,7 +420,11 @@ int sbli_set_state(sbli_grid* g, const double* q, int q_is_host) {
   } else {
     SBLI_TRY(cudaMemcpyAsync(tmp, q, bytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync D2D");
   }
-  SBLI_TRY(launch_to_offset(g->geom, g->ref, tmp, g->reg64[dst], g->stream), "to_offset launch");
+  if (g->precision == SBLI_FP32_DF) {
+    SBLI_TRY(launch_df_split(g->geom.P, g->ref, tmp, reinterpret_cast<float*>(g->reg64[dst]), g->stream), "df_split");
+  } else {
+    SBLI_TRY(launch_to_offset(g->geom, g->ref, tmp, g->reg64[dst], g->stream), "to_offset launch");
+  }
   if (q_is_host) SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
   g->stages_done = 0;
   return SBLI_OK;
@@ -403,7 +436,12 @@ int sbli_get_state(sbli_grid* g, double* q, int q_is_host) {
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "get_state between stages of a step (next stage %d)", g->next_stage);
   const size_t bytes = 5 * (size_t)g->geom.P * sizeof(double);
   double* tmp = g->reg64[(g->state + 1) % g->layout.n64];
-  SBLI_TRY(launch_from_offset(g->geom, g->ref, g->reg64[g->state], tmp, g->stream), "from_offset launch");
+  if (g->precision == SBLI_FP32_DF) {
+    SBLI_TRY(launch_df_join(g->geom.P, g->ref, reinterpret_cast<const float*>(g->reg64[g->state]), tmp, g->stream),
+             "df_join");
+  } else {
+    SBLI_TRY(launch_from_offset(g->geom, g->ref, g->reg64[g->state], tmp, g->stream), "from_offset launch");
+  }
   if (q_is_host) {
     SBLI_TRY(cudaMemcpyAsync(q, tmp, bytes, cudaMemcpyDeviceToHost, g->stream), "cudaMemcpyAsync D2H");
     SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
@@ -425,6 +463,8 @@ int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host) 
       // the register not used by this stage holds nothing live
       for (int r = 0; r < 3; ++r)
         if (g->reg64[r] != p.q_in && g->reg64[r] != p.acc_in) tmp = g->reg64[r];
+    } else if (g->precision == SBLI_FP32_DF) {
+      tmp = g->reg64[g->state];  // Q^n (double-float) is not needed after stage 0
     } else {
       tmp = g->reg64[g->state];  // Q^n is not needed after stage 0
     }
@@ -443,8 +483,18 @@ int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host) 
   };
   if (q_stage)
     if (int rc = copy_out(p.q_in, p.in64, q_stage)) return rc;
-  if (q_acc)
-    if (int rc = copy_out(p.acc_in, true, q_acc)) return rc;
+  if (q_acc) {
+    if (g->precision == SBLI_FP32_DF) {
+      double* tmp = g->reg64[g->state];  // Q^n is not needed after stage 0
+      SBLI_TRY(launch_df_join(g->geom.P, g->ref, p.dacc_in, tmp, g->stream), "df_join");
+      SBLI_TRY(cudaMemcpyAsync(q_acc, tmp, n * sizeof(double),
+                               q_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream),
+               "cudaMemcpyAsync");
+      if (q_is_host) SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
+    } else if (int rc = copy_out(p.acc_in, true, q_acc)) {
+      return rc;
+    }
+  }
   return SBLI_OK;
 }
 
@@ -459,8 +509,9 @@ int sbli_rhs(sbli_grid* g, double* r_dev) {
     a.zc = g->cfg.zc;
     a.q_in = q;
     a.r_out = r_dev;
-    cudaError_t e = g->precision == SBLI_FP64 ? launch_fused_fp64(a, g->cd, g->cfg, true, g->stream)
-                                              : launch_fused_fp32(a, g->cf, g->cfg, true, true, g->stream);
+    cudaError_t e = g->precision == SBLI_FP64      ? launch_fused_fp64(a, g->cd, g->cfg, true, g->stream)
+                    : g->precision == SBLI_FP32_DF ? launch_fused_fp32df(a, g->cf, g->cfg, true, g->stream)
+                                                   : launch_fused_fp32(a, g->cf, g->cfg, true, true, g->stream);
     SBLI_TRY(e, "fused rhs launch");
     return SBLI_OK;
   }
@@ -532,7 +583,15 @@ int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev) {
   if (int rc = check_grid(g)) return rc;
   if (!out_dev) return fail(SBLI_EINVAL, "out_dev is null");
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "kinetic_energy between stages of a step");
-  SBLI_TRY(launch_ke(g->geom, g->cd, g->ref, g->reg64[g->state], g->partials, out_dev, g->stream), "ke launch");
+  const double* q = g->reg64[g->state];
+  if (g->precision == SBLI_FP32_DF) {
+    double* tmp = g->reg64[1 - g->state];  // free at a step boundary
+    const RefState zero{0.0, 0.0};
+    SBLI_TRY(launch_df_join(g->geom.P, zero, reinterpret_cast<const float*>(g->reg64[g->state]), tmp, g->stream),
+             "df_join");
+    q = tmp;
+  }
+  SBLI_TRY(launch_ke(g->geom, g->cd, g->ref, q, g->partials, out_dev, g->stream), "ke launch");
   return SBLI_OK;
 }
 

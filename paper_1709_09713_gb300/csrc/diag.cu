@@ -111,6 +111,35 @@ cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_
   return cudaGetLastError();
 }
 
+__global__ void df_split_kernel(long long n5, long long P, double rho0, double E0, const double* __restrict__ src,
+                                float* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n5; i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / P;
+    const double v = src[i] - (f == 0 ? rho0 : (f == 4 ? E0 : 0.0));
+    const float hi = __double2float_rn(v);
+    dst[i] = hi;
+    dst[i + 5 * P] = __double2float_rn(v - (double)hi);
+  }
+}
+
+__global__ void df_join_kernel(long long n5, long long P, double rho0, double E0, const float* __restrict__ src,
+                               double* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n5; i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / P;
+    dst[i] = ((double)src[i] + (double)src[i + 5 * P]) + (f == 0 ? rho0 : (f == 4 ? E0 : 0.0));
+  }
+}
+
+cudaError_t launch_df_split(long long P, const RefState& r, const double* src, float* dst, cudaStream_t s) {
+  df_split_kernel<<<grid_for(5 * P, 256), 256, 0, s>>>(5 * P, P, r.rho0, r.E0, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_join(long long P, const RefState& r, const float* src, double* dst, cudaStream_t s) {
+  df_join_kernel<<<grid_for(5 * P, 256), 256, 0, s>>>(5 * P, P, r.rho0, r.E0, src, dst);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ KE
 constexpr int KE_BLOCK = 256;
 constexpr int KE_MAX_BLOCKS = 1024;

@@ -29,6 +29,22 @@ cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const Fu
   }
 }
 
+template <int TY>
+static cudaError_t dispatch32df(const StageArgs& a, const Coef<float>& c, bool rhs_only, cudaStream_t s) {
+  if (rhs_only) return launch_fused_t<float, float, float, TY, true, false, false>(a, c, s);
+  if (a.ke_partials) return launch_fused_t<float, float, float, TY, false, true, true>(a, c, s);
+  return launch_fused_t<float, float, float, TY, false, false, true>(a, c, s);
+}
+
+cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
+                                cudaStream_t s) {
+  switch (cfg.ty) {
+    case 8: return dispatch32df<8>(a, c, rhs_only, s);
+    case 16: return dispatch32df<16>(a, c, rhs_only, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg) {
   const long long gx = (g.n0 + TX - 1) / TX, gy = (g.n1 + cfg.ty - 1) / cfg.ty, gz = (g.n2 + cfg.zc - 1) / cfg.zc;
   return (int)(gx * gy * gz);

@@ -182,7 +182,7 @@ constexpr int fused_min_blocks() {
 // Adds the stage input's kinetic energy and enstrophy of the tile's points
 // to ke_acc / ens_acc when WITH_KE.  Ends with a barrier, so the shared
 // memory can be reused by the caller.
-template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false>
 __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c, int bx, int by, int zbeg, int zend_req,
                                             FusedSmem<T, TY>& sm, double& ke_acc, double& ens_acc) {
   using S = FusedSmem<T, TY>;
@@ -340,9 +340,18 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
 
     // accumulator of the centre point, fetched before the arithmetic
     double accv[NF];
+    float dhi[NF], dlo[NF];  // double-float accumulator (DF mode)
     if (!RHS_ONLY && valid_xy) {
+      if (DF) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) accv[f] = accf[f] ? accf[f][o_own] : double(qf[f][o_own]);
+        for (int f = 0; f < NF; ++f) {
+          dhi[f] = a.dacc_in[(long long)f * a.g.P + o_own];
+          dlo[f] = a.dacc_in[(long long)(NF + f) * a.g.P + o_own];
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) accv[f] = accf[f] ? accf[f][o_own] : double(qf[f][o_own]);
+      }
     }
 
     // --------------------------------------------------------------- phase 2b
@@ -440,6 +449,26 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         if (RHS_ONLY) {
 #pragma unroll
           for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o_own] = double(R[f]);
+        } else if (DF) {
+          // binary32 stage, double-float accumulator (hi + lo, binary32
+          // each): acc' = acc + (b dt R) by an error-free two-sum of hi and
+          // the increment, the error folded into lo and renormalised;
+          // Q_{k+1} = hi' + (lo' + (a - b) dt R).
+          const float bdt = float(a.b_dt), ambdt = float(a.amb_dt);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const float r = float(R[f]);
+            const float x = bdt * r;
+            const float s = __fadd_rn(dhi[f], x);
+            const float bb = __fsub_rn(s, dhi[f]);
+            const float err = __fadd_rn(__fsub_rn(dhi[f], __fsub_rn(s, bb)), __fsub_rn(x, bb));
+            const float lo2 = __fadd_rn(dlo[f], err);
+            const float hi3 = __fadd_rn(s, lo2);
+            const float lo3 = __fsub_rn(lo2, __fsub_rn(hi3, s));
+            a.dacc_out[(long long)f * a.g.P + o_own] = hi3;
+            a.dacc_out[(long long)(NF + f) * a.g.P + o_own] = lo3;
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(hi3 + fmaf(ambdt, r, lo3));
+          }
         } else if (sizeof(T) == 8) {
           // binary64 stage: acc + b dt R and acc + a dt R, fused multiply-adds
 #pragma unroll
@@ -499,14 +528,14 @@ __device__ __forceinline__ void block_reduce_pair(double (&red)[2][32], double k
 }
 
 // Single grid: one CTA per (tile, z chunk).
-template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false>
 __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
     fused_stage_kernel(const StageArgs a, const Coef<T> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, TY>& sm = *reinterpret_cast<FusedSmem<T, TY>*>(smem_raw);
   double ke = 0.0, ens = 0.0;
   const int zbeg = blockIdx.z * a.zc;
-  fused_march<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE>(a, c, blockIdx.x, blockIdx.y, zbeg, zbeg + a.zc, sm, ke, ens);
+  fused_march<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF>(a, c, blockIdx.x, blockIdx.y, zbeg, zbeg + a.zc, sm, ke, ens);
   if (WITH_KE) {
     const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     block_reduce_pair<TX * TY>(sm.red, ke, ens, a.ke_partials + 2 * b);
@@ -518,9 +547,9 @@ inline dim3 fused_grid(const Geom& g, int zc) {
   return dim3((g.n0 + TX - 1) / TX, (g.n1 + TY - 1) / TY, (g.n2 + zc - 1) / zc);
 }
 
-template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE>
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false>
 cudaError_t launch_fused_t(const StageArgs& a, const Coef<T>& c, cudaStream_t s) {
-  auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE>;
+  auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF>;
   const size_t smem = sizeof(FusedSmem<T, TY>);
   static bool configured = false;  // one attribute call per instantiation
   if (!configured) {

@@ -67,6 +67,10 @@ struct StageArgs {
   double a_dt, b_dt;       // a_k dt, b_k dt
   double amb_dt;           // (a_k - b_k) dt
   double* ke_partials;     // per-CTA (ke, enstrophy) partial sums, or nullptr
+  // double-float accumulator (precision SBLI_FP32_DF): 5 hi fields then 5 lo
+  // fields of binary32, P values each
+  const float* dacc_in;
+  float* dacc_out;
 };
 
 // Launch configuration chosen for one grid (the autotuner's output).
@@ -82,6 +86,9 @@ cudaError_t launch_fused_fp64(const StageArgs& a, const Coef<double>& c, const F
                               cudaStream_t s);
 cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                               bool rhs_only, cudaStream_t s);
+// binary32 stage with a double-float accumulator (stage inputs are binary32)
+cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
+                                cudaStream_t s);
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg);
 size_t fused_smem_bytes(int elem_bytes, int ty);
 
@@ -92,6 +99,12 @@ cudaError_t launch_from_offset(const Geom& g, const RefState& r, const double* q
                                cudaStream_t s);
 // dst[i] = (double)src[i], i < n
 cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_t s);
+// double-float register (5 hi fields, then 5 lo fields, binary32) <-> binary64
+// state (5 fields).  split: v = src - ref (fields 0 and 4), hi = (float)v,
+// lo = (float)(v - hi); join: dst = ((double)hi + (double)lo) + ref.  Pass a
+// zero RefState to stay in deviation form.
+cudaError_t launch_df_split(long long P, const RefState& r, const double* src, float* dst, cudaStream_t s);
+cudaError_t launch_df_join(long long P, const RefState& r, const float* src, double* dst, cudaStream_t s);
 // KE/enstrophy of a binary64 offset state: per-CTA partials into scratch,
 // then a fixed-order final sum into out[0..1].
 int ke_num_partials(const Geom& g);

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libsbli.so")
 
 SBLI_OK, SBLI_EINVAL, SBLI_ENOMEM, SBLI_ECUDA, SBLI_ETIMEOUT, SBLI_EUNSUPPORTED = range(6)
-SBLI_FP64, SBLI_FP32 = 0, 1
+SBLI_FP64, SBLI_FP32, SBLI_FP32_DF = 0, 1, 2
 SBLI_FUSED, SBLI_STORE_ALL = 0, 1
 
 # Every entry point the header declares, with its ctypes signature.

@@ -276,3 +276,70 @@ def test_fp32_kinetic_energy_history_512_subsample_bound(S, orc):
     assert np.max(np.abs(hb[:, 0] - ha[:, 0]) / ha[:, 0]) <= 1e-6
     errs = rel_fields(b.get_state().cpu().numpy(), a.get_state().cpu().numpy())
     assert max(errs) <= 1e-5, errs
+
+
+# ------------------------------------------------- double-float accumulator
+
+def test_fp32df_state_roundtrip(S):
+    """set/get_state through the double-float register keeps about 48 bits."""
+    n = (24, 16, 12)
+    q = random_state(n, 91)
+    g = S.Grid(n, S.SBLI_FP32_DF, S.SBLI_FUSED)
+    g.set_state(to_dev(q))
+    back = g.get_state().cpu().numpy()
+    assert max(rel_fields(back, q)) <= 1e-13
+
+
+def test_fp32df_against_fp64_oracle(S, orc):
+    n, dt, steps = 32, 1e-3, 10
+    g = S.Grid(n, S.SBLI_FP32_DF, S.SBLI_FUSED)
+    g.init_tgv(1.0)
+    hist = g.step_n_history(steps, dt).cpu().numpy()
+    got = g.get_state().cpu().numpy()
+    p = orc.params(n)
+    q = orc.init_tgv(p)
+    for s_ in range(steps):
+        ke_o, _ = orc.ke_enstrophy(p, q)
+        assert abs(hist[s_, 0] - ke_o) / ke_o <= 1e-6
+        q = orc.step(p, q, dt, 1)
+    errs = rel_fields(got, q)
+    assert max(errs) <= 1e-5, errs
+    ke, _ = g.kinetic_energy()
+    assert abs(ke - orc.ke_enstrophy(p, q)[0]) / ke <= 1e-6
+
+
+def test_fp32df_rhs_stages_and_graph(S, orc):
+    n, dt = (40, 24, 20), 1e-3
+    q = random_state(n, 17)
+    g = S.Grid(n, S.SBLI_FP32_DF, S.SBLI_FUSED)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    assert max(rel_fields(r, orc.rhs(orc.params(n), q))) <= 1e-4
+    p = orc.params(n)
+    g.rk_stage(0, dt)
+    qs, qa = (t.cpu().numpy() for t in g.get_stage())
+    q1, acc1 = orc.stage(p, 0, dt, q, q)
+    assert max(rel_fields(qs, q1)) <= 1e-6 and max(rel_fields(qa, acc1)) <= 1e-6
+    g.rk_stage(1, dt)
+    g.rk_stage(2, dt)
+    a = S.Grid(n, S.SBLI_FP32_DF, S.SBLI_FUSED)
+    b = S.Grid(n, S.SBLI_FP32_DF, S.SBLI_FUSED)
+    a.set_state(to_dev(q))
+    b.set_state(to_dev(q))
+    a.step_n(7, dt)
+    for _ in range(7):
+        for k in range(3):
+            b.rk_stage(k, dt)
+    assert torch.equal(a.get_state(), b.get_state())
+    with pytest.raises(S.SbliError) as e:
+        S.sbli_workspace_bytes(16, 16, 16, S.SBLI_FP32_DF, S.SBLI_STORE_ALL)
+    assert e.value.code == S.SBLI_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_init_then_get_state_every_precision(S, orc, precision):
+    n = (20, 12, 8)
+    g = S.Grid(n, precision, S.SBLI_FUSED)
+    g.init_tgv(0.97)
+    got = g.get_state().cpu().numpy()
+    assert max(rel_fields(got, orc.init_tgv(orc.params(n), 0.97))) <= 1e-14
