@@ -169,18 +169,23 @@ SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, in
                                          void* stream);
 
 /* Launch configuration of the fused kernel: in-plane tile height (the tile
- * is 32 x tile_y points; binary64 grids use 8, binary32 grids 8 or 16) and
- * planes per CTA along x2 (>= 4).  set_config validates and applies it
- * (cached step graphs are rebuilt); must be called at a step boundary. */
-SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta);
-SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta);
+ * is 32 x tile_y points; binary64 grids use 8, binary32 grids 8 or 16),
+ * planes per CTA along x2 (>= 4) and, for the binary32 paths, where each
+ * thread keeps its column's records of the five x2 planes (z_queue = 0: the
+ * shared-memory ring; 1: a per-thread queue in Blackwell tensor memory).
+ * set_config validates and applies it (cached step graphs are rebuilt); must
+ * be called at a step boundary.  z_queue may be NULL in get_config. */
+SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue);
+SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue);
 
-/* Autotuner: times candidate configurations (each allowed tile height with
- * the planes-per-CTA values a wave-balance model ranks best) on this grid with
+/* Autotuner: times candidate configurations (each allowed tile height and
+ * z queue with the planes-per-CTA values a wave-balance model ranks best) on
+ * this grid with
  * `reps` timed stage-0 launches each, which read the state and write only the
  * scratch registers, keeps the fastest and returns it.  The state is not
  * changed.  Synchronises the grid's stream.  Fused variant only. */
-SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, float* best_stage_ms);
+SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue,
+                           float* best_stage_ms);
 
 /* ---------------------------------------------------------------------
  * Batched ensembles: up to 64 members (each its own grid size, Re, M, Pr,

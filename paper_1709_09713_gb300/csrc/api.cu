@@ -154,15 +154,16 @@ void rank_zc(const Geom& g, int precision, int ty, int* best, int nbest) {
 FusedConfig default_config(const Geom& g, int precision) {
   FusedConfig cfg;
   cfg.ty = 8;
+  cfg.zq = 0;
   int zc[1];
   rank_zc(g, precision, cfg.ty, zc, 1);
   cfg.zc = std::max(4, std::min(zc[0], g.n2));
   return cfg;
 }
 
-bool valid_config(int precision, int ty, int zc) {
-  if (zc < 4) return false;
-  if (precision == SBLI_FP64) return ty == 8;
+bool valid_config(int precision, int ty, int zc, int zq = 0) {
+  if (zc < 4 || zq < 0 || zq > 1) return false;
+  if (precision == SBLI_FP64) return ty == 8 && zq == 0;
   return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
 }
 
@@ -607,47 +608,51 @@ int sbli_kinetic_energy(sbli_grid* g, double* ke, double* enstrophy) {
   return SBLI_OK;
 }
 
-int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta) {
+int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue) {
   if (!g || !tile_y || !planes_per_cta) return fail(SBLI_EINVAL, "null argument");
   *tile_y = g->cfg.ty;
   *planes_per_cta = g->cfg.zc;
+  if (z_queue) *z_queue = g->cfg.zq;
   return SBLI_OK;
 }
 
-int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta) {
+int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue) {
   if (int rc = check_grid(g)) return rc;
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "set_config between stages of a step");
-  if (!valid_config(g->precision, tile_y, planes_per_cta))
-    return fail(SBLI_EINVAL, "config tile_y=%d planes_per_cta=%d not available for this precision", tile_y,
-                planes_per_cta);
+  if (!valid_config(g->precision, tile_y, planes_per_cta, z_queue) || (z_queue && g->variant != SBLI_FUSED))
+    return fail(SBLI_EINVAL, "config tile_y=%d planes_per_cta=%d z_queue=%d not available for this grid", tile_y,
+                planes_per_cta, z_queue);
   FusedConfig cfg;
   cfg.ty = tile_y;
   cfg.zc = std::min(planes_per_cta, g->geom.n2);
-  if (cfg.ty != g->cfg.ty || cfg.zc != g->cfg.zc) {
+  cfg.zq = z_queue;
+  if (cfg.ty != g->cfg.ty || cfg.zc != g->cfg.zc || cfg.zq != g->cfg.zq) {
     g->cfg = cfg;
     drop_graphs(g);
   }
   return SBLI_OK;
 }
 
-int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, float* best_stage_ms) {
+int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue, float* best_stage_ms) {
   if (int rc = check_grid(g)) return rc;
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "autotune between stages of a step");
   if (g->variant != SBLI_FUSED) return fail(SBLI_EUNSUPPORTED, "autotune needs the fused variant");
   if (reps < 1) return fail(SBLI_EINVAL, "reps must be >= 1");
-  FusedConfig cand[8];
+  FusedConfig cand[16];
   int nc = 0;
   const int tys[2] = {8, 16};
-  for (int t = 0; t < 2; ++t) {
-    if (!valid_config(g->precision, tys[t], 4)) continue;
-    int zc[3];
-    rank_zc(g->geom, g->precision, tys[t], zc, 3);
-    for (int i = 0; i < 3; ++i) {
-      bool dup = false;
-      for (int j = 0; j < nc; ++j) dup |= (cand[j].ty == tys[t] && cand[j].zc == zc[i]);
-      if (!dup && nc < 8) cand[nc++] = FusedConfig{tys[t], std::max(4, std::min(zc[i], g->geom.n2))};
+  for (int zq = 0; zq < 2; ++zq)
+    for (int t = 0; t < 2; ++t) {
+      if (!valid_config(g->precision, tys[t], 4, zq)) continue;
+      int zc[3];
+      rank_zc(g->geom, g->precision, tys[t], zc, 3);
+      for (int i = 0; i < 3; ++i) {
+        bool dup = false;
+        const int z = std::max(4, std::min(zc[i], g->geom.n2));
+        for (int j = 0; j < nc; ++j) dup |= (cand[j].ty == tys[t] && cand[j].zc == z && cand[j].zq == zq);
+        if (!dup && nc < 16) cand[nc++] = FusedConfig{tys[t], z, zq};
+      }
     }
-  }
   cudaEvent_t e0, e1;
   SBLI_TRY(cudaEventCreate(&e0), "cudaEventCreate");
   cudaError_t ce = cudaEventCreate(&e1);
@@ -682,9 +687,10 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, floa
     return cuda_fail(err, "autotune launch");
   }
   g->cfg = cand[best];
-  if (g->cfg.ty != saved.ty || g->cfg.zc != saved.zc) drop_graphs(g);
+  if (g->cfg.ty != saved.ty || g->cfg.zc != saved.zc || g->cfg.zq != saved.zq) drop_graphs(g);
   if (tile_y) *tile_y = g->cfg.ty;
   if (planes_per_cta) *planes_per_cta = g->cfg.zc;
+  if (z_queue) *z_queue = g->cfg.zq;
   if (best_stage_ms) *best_stage_ms = best_ms;
   return SBLI_OK;
 }

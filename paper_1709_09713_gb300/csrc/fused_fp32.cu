@@ -22,6 +22,7 @@ static cudaError_t dispatch32(const StageArgs& a, const Coef<float>& c, bool in_
 
 cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                               bool rhs_only, cudaStream_t s) {
+  if (cfg.zq) return launch_fused_fp32_tmem(a, c, cfg, in_fp64, false, rhs_only, s);
   switch (cfg.ty) {
     case 8: return dispatch32<8>(a, c, in_fp64, rhs_only, s);
     case 16: return dispatch32<16>(a, c, in_fp64, rhs_only, s);
@@ -38,6 +39,7 @@ static cudaError_t dispatch32df(const StageArgs& a, const Coef<float>& c, bool r
 
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s) {
+  if (cfg.zq) return launch_fused_fp32_tmem(a, c, cfg, false, true, rhs_only, s);
   switch (cfg.ty) {
     case 8: return dispatch32df<8>(a, c, rhs_only, s);
     case 16: return dispatch32df<16>(a, c, rhs_only, s);

@@ -55,6 +55,7 @@ struct FusedSmem {
   T s0buf[TY][SX];            // s_0 = D1_y u1 + D1_z u2, centre plane, x0-haloed rows
   T s1buf[SY][TX];            // s_1 = D1_x u0 + D1_z u2, centre plane, x1-haloed columns
   double red[2][32];          // block reduction of (ke, enstrophy)
+  uint32_t tmem_base;         // TMEM allocation (z queue variant)
 };
 
 template <typename T>
@@ -96,6 +97,83 @@ __device__ __forceinline__ void store_rec(double* p, const double (&r)[NV]) {
   for (int i = 0; i < NV / 2; ++i) q[i] = make_double2(r[2 * i], r[2 * i + 1]);
 }
 
+// ---- tensor memory (TMEM) as a per-thread queue of x2-neighbour records.
+// Each warp of the CTA owns the 32 TMEM lanes of its quarter (warp % 4) and a
+// 64-column window (warp / 4); a thread keeps its own column's records of the
+// five ring planes there: fields 0-7 of slot s in columns 8s .. 8s+7, fields
+// 8-9 in columns 40+2s, 41+2s, so every access is aligned to its own width.
+// 32x32b shapes: each thread of the warp reads or writes its own lane.
+constexpr int TM_COLS_PER_WARP = 64;
+constexpr int TM_TAIL = 8 * NSLOT;
+static_assert(NV == 10 && TM_TAIL + 2 * NSLOT <= TM_COLS_PER_WARP, "z queue must fit the warp's TMEM window");
+
+template <int NW>
+constexpr int tmem_columns() {
+  return TM_COLS_PER_WARP * ((NW + 3) / 4) < 32 ? 32 : TM_COLS_PER_WARP * ((NW + 3) / 4);
+}
+
+// win: this thread's window address (lane and window column), slot: ring slot
+__device__ __forceinline__ void tmem_store_rec(uint32_t win, int slot, const float (&r)[NV]) {
+  const uint32_t taddr = win + (uint32_t)(8 * slot), ttail = win + (uint32_t)(TM_TAIL + 2 * slot);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x2.b32 [%9], {%10, %11};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "r"(__float_as_uint(r[0])), "r"(__float_as_uint(r[1])), "r"(__float_as_uint(r[2])), "r"(__float_as_uint(r[3])),
+      "r"(__float_as_uint(r[4])), "r"(__float_as_uint(r[5])), "r"(__float_as_uint(r[6])), "r"(__float_as_uint(r[7])),
+      "r"(ttail), "r"(__float_as_uint(r[8])), "r"(__float_as_uint(r[9]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, float (&r)[NV]) {
+  const uint32_t taddr = win + (uint32_t)(8 * slot), ttail = win + (uint32_t)(TM_TAIL + 2 * slot);
+  uint32_t v[NV];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%10];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%11];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9])
+      : "r"(taddr), "r"(ttail)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < NV; ++i) r[i] = __uint_as_float(v[i]);
+}
+__device__ __forceinline__ void tmem_load_rec(uint32_t, int, double (&)[NV]) {}
+__device__ __forceinline__ void tmem_store_rec(uint32_t, int, const double (&)[NV]) {}
+
+// Allocate / release the CTA's TMEM columns (warp 0), publishing the base
+// address through shared memory.  The column budget per SM (at most 256 with
+// these kernels' shared-memory footprints) is below the 512 available, so the
+// allocation never waits.
+template <int NCOL>
+__device__ __forceinline__ uint32_t tmem_acquire(uint32_t* smem_slot) {
+  if ((threadIdx.x >> 5) == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(NCOL) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *(volatile uint32_t*)smem_slot;
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_release(uint32_t base) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(NCOL) : "memory");
+}
+
+// This thread's TMEM window: lane quarter of its warp, column window warp / 4.
+__device__ __forceinline__ uint32_t tmem_window(uint32_t base) {
+  const uint32_t w = threadIdx.x >> 5;
+  return base + (((w & 3u) * 32u) << 16) + (w >> 2) * (uint32_t)TM_COLS_PER_WARP;
+}
+
 // Stage input value in the arithmetic type (binary64 inputs to a binary32
 // stage are narrowed with integer re-packing, see fpconv.cuh).
 template <typename T, typename TIN>
@@ -124,18 +202,18 @@ struct Terms {
   T G[3];      // sum_j d2 u_j / dx_i dx_j (Eq. 7 on j = i, D1 o D1 otherwise)
 };
 
-// All derivatives along axis A at one point.  nbp(k) points at the record of
+// All derivatives along axis A at one point.  ldrec(k, r) loads the record of
 // the neighbour k = 0..3 (offsets -2, -1, +1, +2 along A); uc are the centre
 // velocities; sfun(k, record) gives the mixed-term helper s_A at neighbour k.
-template <int A, typename T, typename NBP, typename SF>
-__device__ __forceinline__ void axis_terms(const NBP& nbp, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
+template <int A, typename T, typename LD, typename SF>
+__device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
                                            Terms<T>& t) {
   const T c1 = c.c1[A], c2 = c.c2[A], e0 = c.e0[A], e1 = c.e1[A], e2 = c.e2[A];
   auto d1 = [&](T fm2, T fm1, T fp1, T fp2) { return c1 * (fp1 - fm1) - c2 * (fp2 - fm2); };
 
   T r[4][NV];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) load_rec(nbp(k), r[k]);
+  for (int k = 0; k < 4; ++k) ldrec(k, r[k]);
   T s[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) s[k] = sfun(k, r[k]);
@@ -182,14 +260,17 @@ constexpr int fused_min_blocks() {
 // Adds the stage input's kinetic energy and enstrophy of the tile's points
 // to ke_acc / ens_acc when WITH_KE.  Ends with a barrier, so the shared
 // memory can be reused by the caller.
-template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false>
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
+          bool ZT = false>
 __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c, int bx, int by, int zbeg, int zend_req,
-                                            FusedSmem<T, TY>& sm, double& ke_acc, double& ens_acc) {
+                                            FusedSmem<T, TY>& sm, double& ke_acc, double& ens_acc,
+                                            uint32_t tmem_base = 0) {
   using S = FusedSmem<T, TY>;
   constexpr int SY = S::SY;
   constexpr int NT = TX * TY;
   constexpr int PTS = SX * SY;
-  constexpr int LPT = (PTS + NT - 1) / NT;
+  constexpr int NHALO = PTS - NT;                  // haloed points outside the tile
+  constexpr int LPT = 1 + (NHALO + NT - 1) / NT;   // own point + halo points per thread
 
   const int n0 = a.g.n0, n1 = a.g.n1, n2 = a.g.n2;
   const unsigned plane = (unsigned)n0 * (unsigned)n1;
@@ -209,15 +290,33 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     accf[f] = a.acc_in ? a.acc_in + (long long)f * a.g.P : nullptr;
   }
 
-  // haloed points this thread loads on every plane (periodic wrap)
+  // points this thread loads on every plane (periodic wrap): its own tile
+  // point first, then at most LPT-1 points of the halo ring (the two rows
+  // above and below the tile at full haloed width, then the two columns on
+  // each side of the tile rows)
   int ld_off[LPT], ld_s[LPT];
 #pragma unroll
   for (int l = 0; l < LPT; ++l) {
-    const int idx = tid + l * NT;
-    if (idx < PTS) {
-      const int sy = idx / SX, sx = idx % SX;
+    int sy = -1, sx = -1;
+    if (l == 0) {
+      sy = ty + HALO;
+      sx = tx + HALO;
+    } else {
+      const int h = tid + (l - 1) * NT;
+      if (h < 4 * SX) {
+        const int r = h / SX;
+        sy = (r < 2) ? r : TY + r;
+        sx = h % SX;
+      } else if (h < NHALO) {
+        const int h2 = h - 4 * SX;
+        const int k = h2 & 3;
+        sy = HALO + (h2 >> 2);
+        sx = (k < 2) ? k : TX + k;
+      }
+    }
+    if (sy >= 0) {
       ld_off[l] = wrapi(x0 - HALO + sx, n0) + n0 * wrapi(y0 - HALO + sy, n1);
-      ld_s[l] = idx;
+      ld_s[l] = sy * SX + sx;
     } else {
       ld_off[l] = -1;
       ld_s[l] = 0;
@@ -226,6 +325,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
 
   const int nplanes = zend - zbeg;
   const int nit = nplanes + 4;
+  const uint32_t twin = ZT ? tmem_window(tmem_base) : 0u;
   T d22 = T(0);
 
   // halo tasks of phase 2b, fixed for the whole z march: s_0 on the x0-halo
@@ -289,7 +389,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       T* ring = &sm.ring[se][0][0][0];
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        if (ld_off[l] >= 0) {
+        if (l == 0 || ld_off[l] >= 0) {  // the own point is always loaded
           T rec[NV];
           const T rho_p = to_compute<T, TIN>(pf[l][0]);
           const T m0 = to_compute<T, TIN>(pf[l][1]);
@@ -312,6 +412,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           rec[V_P] = p_p;
           rec[V_T] = T_p;
           store_rec(ring + ld_s[l] * NV, rec);
+          if (ZT && l == 0) tmem_store_rec(twin, se, rec);  // l == 0: every thread
         }
       }
     }
@@ -386,7 +487,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       const int sy = ty + HALO, sx = tx + HALO;
       const T(*C)[SX][NV] = sm.ring[scen];
       T cen[NV];
-      load_rec(&C[sy][sx][0], cen);
+      if (ZT) tmem_load_rec(twin, scen, cen);
+      else load_rec(&C[sy][sx][0], cen);
       const T rho_p = cen[V_RHO];
       const T mc[3] = {cen[V_M0], cen[V_M1], cen[V_M2]};
       const T Ec = cen[V_E];
@@ -407,21 +509,24 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       // x0 group first (SN2 ordering), then x1, x2
       {
         const int off[4] = {-2, -1, 1, 2};
-        auto nbp = [&](int k) { return &C[sy][sx + off[k]][0]; };
+        auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy][sx + off[k]][0], r); };
         auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[ty][sx + off[k]]; };
-        axis_terms<0>(nbp, sf, c, uc, t);
+        axis_terms<0>(ld, sf, c, uc, t);
       }
       {
         const int off[4] = {-2, -1, 1, 2};
-        auto nbp = [&](int k) { return &C[sy + off[k]][sx][0]; };
+        auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy + off[k]][sx][0], r); };
         auto sf = [&](int k, const T(&)[NV]) { return sm.s1buf[sy + off[k]][tx]; };
-        axis_terms<1>(nbp, sf, c, uc, t);
+        axis_terms<1>(ld, sf, c, uc, t);
       }
       {
         const int zs[4] = {sl[0], sl[1], sl[3], sl[4]};
-        auto nbp = [&](int k) { return &sm.ring[zs[k]][sy][sx][0]; };
+        auto ld = [&](int k, T(&r)[NV]) {
+          if (ZT) tmem_load_rec(twin, zs[k], r);
+          else load_rec(&sm.ring[zs[k]][sy][sx][0], r);
+        };
         auto sf = [&](int k, const T(&)[NV]) { return sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx]; };
-        axis_terms<2>(nbp, sf, c, uc, t);
+        axis_terms<2>(ld, sf, c, uc, t);
       }
 
       // assemble Eqs. 1-3
@@ -527,19 +632,25 @@ __device__ __forceinline__ void block_reduce_pair(double (&red)[2][32], double k
   __syncthreads();
 }
 
-// Single grid: one CTA per (tile, z chunk).
-template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false>
+// Single grid: one CTA per (tile, z chunk).  ZT: x2-neighbour records in TMEM.
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
+          bool ZT = false>
 __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
     fused_stage_kernel(const StageArgs a, const Coef<T> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, TY>& sm = *reinterpret_cast<FusedSmem<T, TY>*>(smem_raw);
+  constexpr int NCOL = tmem_columns<TY>();  // TX*TY/32 = TY warps
+  uint32_t tbase = 0;
+  if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
   double ke = 0.0, ens = 0.0;
   const int zbeg = blockIdx.z * a.zc;
-  fused_march<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF>(a, c, blockIdx.x, blockIdx.y, zbeg, zbeg + a.zc, sm, ke, ens);
+  fused_march<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF, ZT>(a, c, blockIdx.x, blockIdx.y, zbeg, zbeg + a.zc, sm, ke,
+                                                          ens, tbase);
   if (WITH_KE) {
     const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     block_reduce_pair<TX * TY>(sm.red, ke, ens, a.ke_partials + 2 * b);
   }
+  if (ZT) tmem_release<NCOL>(tbase);
 }
 
 template <int TY>
@@ -547,9 +658,10 @@ inline dim3 fused_grid(const Geom& g, int zc) {
   return dim3((g.n0 + TX - 1) / TX, (g.n1 + TY - 1) / TY, (g.n2 + zc - 1) / zc);
 }
 
-template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false>
+template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
+          bool ZT = false>
 cudaError_t launch_fused_t(const StageArgs& a, const Coef<T>& c, cudaStream_t s) {
-  auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF>;
+  auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF, ZT>;
   const size_t smem = sizeof(FusedSmem<T, TY>);
   static bool configured = false;  // one attribute call per instantiation
   if (!configured) {

@@ -77,6 +77,8 @@ struct StageArgs {
 struct FusedConfig {
   int ty;  // in-plane tile height (tile is 32 x ty)
   int zc;  // planes per CTA
+  int zq;  // binary32 paths: 0 = x2-neighbour records from the shared-memory
+           // ring, 1 = from a per-thread queue in tensor memory (TMEM)
 };
 
 // Host launchers (defined in fused_fp64.cu / fused_fp32.cu).
@@ -89,6 +91,9 @@ cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const Fu
 // binary32 stage with a double-float accumulator (stage inputs are binary32)
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s);
+// the same two binary32 paths with the TMEM z queue (fused_fp32_tmem.cu)
+cudaError_t launch_fused_fp32_tmem(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
+                                   bool df, bool rhs_only, cudaStream_t s);
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg);
 size_t fused_smem_bytes(int elem_bytes, int ty);
 

@@ -229,17 +229,26 @@ def test_error_paths_fault_nothing(S):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("precision,configs", [(1, [(8, 4), (8, 13), (16, 7), (16, 40)]), (0, [(8, 4), (8, 9), (8, 40)])])
+@pytest.mark.parametrize(
+    "precision,configs",
+    [
+        (1, [(8, 4, 0), (8, 13, 0), (16, 7, 0), (16, 40, 0), (8, 13, 1), (16, 7, 1), (16, 40, 1), (8, 4, 1)]),
+        (2, [(8, 4, 0), (16, 7, 0), (8, 13, 1), (16, 40, 1)]),
+        (0, [(8, 4, 0), (8, 9, 0), (8, 40, 0)]),
+    ],
+)
 def test_launch_configs_are_bitwise_identical(S, precision, configs):
-    """Tile height and planes per CTA change only the work decomposition:
-    every point's arithmetic is the same, so the state is bitwise equal."""
+    """Tile height, planes per CTA and where the x2-neighbour records live
+    (shared-memory ring or TMEM queue) change only the work decomposition and
+    data movement: every point's arithmetic is the same, so the state is
+    bitwise equal."""
     n, dt = (64, 48, 40), 1e-3
     q = to_dev(random_state(n, 23))
     ref = None
-    for ty, zc in configs:
+    for ty, zc, zq in configs:
         g = S.Grid(n, precision, S.SBLI_FUSED)
-        g.set_config(ty, zc)
-        assert g.config() == (ty, min(zc, n[2]))
+        g.set_config(ty, zc, zq)
+        assert g.config() == (ty, min(zc, n[2]), zq)
         g.set_state(q)
         g.step_n(2, dt)
         out = g.get_state()
@@ -254,13 +263,18 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     g = S.Grid(n, S.SBLI_FP32, S.SBLI_FUSED)
     g.init_tgv()
     before = g.get_state()
-    ty, zc, ms = g.autotune(reps=2)
-    assert ty in (8, 16) and 4 <= zc <= n[2] and ms > 0
+    ty, zc, zq, ms = g.autotune(reps=2)
+    assert ty in (8, 16) and 4 <= zc <= n[2] and zq in (0, 1) and ms > 0
     assert torch.equal(g.get_state(), before)
-    assert g.config() == (ty, zc)
+    assert g.config() == (ty, zc, zq)
     g.step_n(1, 1e-3)
     with pytest.raises(S.SbliError):
         g.set_config(12, 8)
+    with pytest.raises(S.SbliError):
+        g.set_config(8, 8, 2)
+    d = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
+    with pytest.raises(S.SbliError):
+        d.set_config(8, 8, 1)  # the TMEM queue holds binary32 records only
 
 
 def test_fp32_kinetic_energy_history_512_subsample_bound(S, orc):
