@@ -72,6 +72,32 @@ def perturbation(n, seed: int, scale: float, kmax: int = 4) -> np.ndarray:
     return np.stack([scale * smooth_field(n, rng, kmax=kmax) for _ in range(5)])
 
 
+def separable_perturbation(n, seed: int, scale: float, modes: int = 2, kmax: int = 4) -> np.ndarray:
+    """A smooth random perturbation of all five fields, cheap at large N: each
+    field is ``scale`` times a sum of ``modes`` products a(x0) b(x1) c(x2) of
+    random 1-D trigonometric polynomials (wavenumbers 1..kmax, random phases),
+    shape (5, n2, n1, n0).  Breaks the Taylor-Green symmetries."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    rng = np.random.default_rng(seed)
+    axes = _grid_axes(n)
+
+    def series(x):
+        out = np.zeros_like(x)
+        for kw in range(1, kmax + 1):
+            out += rng.uniform(-1.0, 1.0) / kw * np.cos(kw * x + rng.uniform(0.0, 2.0 * math.pi))
+        return out
+
+    q = np.zeros((5, n[2], n[1], n[0]))
+    tmp = np.empty((n[2], n[1], n[0]))
+    for f in range(5):
+        for _ in range(modes):
+            a, b, c = (series(x) for x in axes)
+            np.multiply(((scale / modes) * c)[:, None, None], np.multiply.outer(b, a)[None, :, :], out=tmp)
+            q[f] += tmp
+    return q
+
+
 @dataclass
 class EnsembleMember:
     n: int
