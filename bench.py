@@ -48,12 +48,17 @@ FP64_FLOP_PER_CLK_PER_SM = 4.0
 # the three stages of a step (minimum traffic of the two-register scheme):
 #   binary64: 50 values per point-step / 3 * 8 B = 133.3 B
 #   binary32 stage fields + binary64 accumulator: 320 B / 3 = 106.7 B
-ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}
+ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "df64": 400.0 / 3.0}
 # binary64 flop per point-stage the fused kernel executes (2 DFMA + DADD +
 # DMUL), counted by ncu on the 256^3 stage-1 launch (profiles/).
 FUSED_FP64_FLOP_PER_PT = 512.3
-# DRAM bytes per launch from the same ncu captures (None once stale)
-NCU_TRAFFIC = {("fp64", 256): 2.692e9, ("fp32", 256): 1.980e9}
+# DRAM bytes per launch (stage-1 launch: 160 B/pt algorithmic) from the ncu
+# captures summarised in profiles/ (an entry is removed once its kernel changes)
+NCU_TRAFFIC = {("fp64", 256): 2.692e9}
+# thread instructions per point-stage of the double-float kernel (ncu,
+# smsp__inst_executed x 32 / points); its ceiling is one warp instruction per
+# clock per SM sub-partition
+DF64_INST_PER_PT = 5335.0
 
 
 def parse():
@@ -65,6 +70,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--variant", default="fused", choices=["fused", "store_all"])
+    ap.add_argument("--alg-steps", type=int, default=24,
+                    help="steps per algorithm class in the comparison leg (>= ~1 s each for NVML energy)")
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--solve-steps", type=int, default=10, help="time steps per e2e solve")
     ap.add_argument("--e2e-reps", type=int, default=2)
@@ -76,7 +83,46 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--profile", choices=["stage", "algorithms"], default=None,
+                    help="untimed runs for ncu: 'stage' = --steps steps of one grid (--n, --profile-precision, "
+                         "--profile-variant) stage by stage; 'algorithms' = stage 0 of every binary64 "
+                         "algorithm class at --n")
+    ap.add_argument("--profile-precision", default="fp64", choices=sorted(PRECISIONS))
+    ap.add_argument("--profile-variant", default="fused", choices=sorted(VARIANTS))
+    ap.add_argument("--profile-config", default=None, help="tile_y,planes_per_cta,z_queue (default: the grid's)")
     return ap.parse_args()
+
+
+def run_profile(args):
+    """Work for profiler captures: no timing, prints "ok"."""
+    import torch
+
+    from paper_1709_09713_gb300 import build as B
+    from paper_1709_09713_gb300 import sbli as S
+
+    if not os.path.exists(S.LIB_PATH):
+        B.build()
+    S.lib()
+    if args.profile == "stage":
+        g = S.Grid(args.n, PRECISIONS[args.profile_precision], VARIANTS[args.profile_variant])
+        if args.profile_config:
+            g.set_config(*(int(x) for x in args.profile_config.split(",")))
+        g.init_tgv(1.0)
+        for _ in range(args.steps):
+            for k in range(3):
+                g.rk_stage(k, args.dt)
+        torch.cuda.synchronize()
+        g.close()
+    else:
+        for name in ("store_all", "RS", "SS", "RA", "SN", "SN2", "fused"):
+            g = S.Grid(args.n, S.SBLI_FP64, VARIANTS[name])
+            g.init_tgv(1.0)
+            g.rk_stage(0, args.dt)
+            torch.cuda.synchronize()
+            g.close()
+            del g
+            torch.cuda.empty_cache()
+    print("ok")
 
 
 # ------------------------------------------------------------ clocks, NVML
@@ -313,10 +359,11 @@ def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, aren
             "offered_pt_stage_per_s": sum(3.0 * q.n**3 * q.steps for q in trace) / max(trace[-1].arrival_s, 1e-9)}
 
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2, "df64": 3}
+VARIANTS = {"fused": 0, "store_all": 1, "RS": 2, "SS": 3, "RA": 4, "SN": 5, "SN2": 6}
 
 
-def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False):
+def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=None):
     """Throughput of one extra configuration (no e2e, no clocks)."""
     import torch
 
@@ -340,10 +387,53 @@ def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False):
            "autotuned": bool(tune)}
     if variant == "fused":
         peaks, kind = measured_peaks()
-        ach = ALG_BYTES["fp64" if precision == "fp64" else "fp32"] * P / (stage_ms / 1e3) / 1e9
+        ach = ALG_BYTES[precision] * P / (stage_ms / 1e3) / 1e9
         out["hbm"] = {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                       "peak_source": kind}
+        if precision == "df64" and DF64_INST_PER_PT and clock_ghz:
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            peak = sms * 4 * 32 * clock_ghz * 1e9
+            rate = DF64_INST_PER_PT * P / (stage_ms / 1e3)
+            out["issue"] = {"achieved": rate, "peak": peak, "unit": "thread-instr/s", "frac": rate / peak,
+                            "note": f"{DF64_INST_PER_PT:.0f} instructions per pt-stage (ncu); peak = {sms} SMs x 4 "
+                                    f"sub-partitions x 32 lanes x {clock_ghz:.3f} GHz"}
     return out
+
+
+def algorithms_leg(S, n, steps, warmup, dt, ws, nvml):
+    """The paper's algorithm classes (section 2.3) on the binary64 Taylor-Green
+    vortex: the tiled fused kernel, store-all (BL), intermediate storage (RS,
+    SS) and one-thread-per-point minimal storage (RA, SN, SN2).  Throughput,
+    joules per pt-stage (NVML energy over each timed region), and speed-up and
+    energy saving relative to BL as the paper tabulates them."""
+    import torch
+
+    rows = []
+    for var in (S.SBLI_STORE_ALL, S.SBLI_RS, S.SBLI_SS, S.SBLI_RA, S.SBLI_SN, S.SBLI_SN2, S.SBLI_FUSED):
+        stream = torch.cuda.Stream()
+        g = S.Grid(n, S.SBLI_FP64, var, stream=stream)
+        with torch.cuda.stream(stream):
+            g.init_tgv(1.0)
+            g.step_n(warmup, dt)
+        stream.synchronize()
+        e0 = nvml.energy_mj() if nvml.ok else None
+        ms = time_steps(S, g, stream, steps, dt, ws)
+        e1 = nvml.energy_mj() if nvml.ok else None
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+        pts = 3.0 * n**3 * steps
+        row = {"algorithm": S.VARIANT_NAMES[var], "value": pts * ws / (ms / 1e3), "stage_ms": ms / (3 * steps)}
+        if e0 is not None and e1 is not None:
+            row["j_per_pt_stage"] = (e1 - e0) / 1e3 / pts
+        rows.append(row)
+    bl = rows[0]
+    for r in rows:
+        r["speedup_vs_bl"] = bl["stage_ms"] / r["stage_ms"]
+        if "j_per_pt_stage" in r and "j_per_pt_stage" in bl:
+            r["energy_saving_vs_bl"] = bl["j_per_pt_stage"] / r["j_per_pt_stage"]
+    return {"workload": f"TGV {n}^3 fp64, Re 1600, M 0.1, dt {dt}: the paper's algorithm classes",
+            "unit": "pt-stage/s", "steps": steps, "rows": rows}
 
 
 # ------------------------------------------------------------- our arm
@@ -455,9 +545,11 @@ def run_ours(args):
         line["energy"] = {"joules": joules, "j_per_pt_stage": joules / (3.0 * P * args.steps),
                           "source": "nvmlDeviceGetTotalEnergyConsumption delta over the timed region"}
     if not args.no_legs:
-        line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
+        cg = (clk.get("sm_mhz") or 2070.0) / 1e3
+        line["legs"] = [leg(S, 256, "df64", "fused", args.leg_steps, 2, dt, ws, clock_ghz=cg),
+                        leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
                         leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
-                        leg(S, 256, "fp64", "store_all", max(3, args.leg_steps // 4), 1, dt, ws),
+                        algorithms_leg(S, 256, args.alg_steps, 1, dt, ws, nvml),
                         ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi)]
     if rank == 0 and not args.no_cpu_baseline:
@@ -501,7 +593,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -29,13 +29,26 @@
  *    and the state between steps are double-float pairs (hi + lo, two
  *    binary32, about 48 significant bits) updated with error-free binary32
  *    additions, so no binary64 arithmetic runs in the stages (fused variant,
- *    single grids only).  All store the state as deviations from the uniform
+ *    single grids only).  Precision SBLI_DF64: binary64 registers, state and
+ *    accumulator exactly as SBLI_FP64, but the stage arithmetic (primitives,
+ *    derivatives, residual) in double-float: each value a hi + lo pair of
+ *    binary32 (about 48 significant bits) evaluated on the binary32 pipe with
+ *    error-free transformations; the RK update is the binary64 FMA (fused
+ *    variant, single grids only).  All store the state as deviations from the uniform
  *    reference state (rho = 1, u = 0, p = 1/(gamma M^2)); the
  *    get/set calls convert to and from the plain conserved variables.
  *  - Variant SBLI_FUSED evaluates every derivative on the fly and writes the
- *    stage update in the same kernel (the "store none" class of §2.5, with
- *    the RK update of Fig. 1 fused in).  Variant SBLI_STORE_ALL stores each
- *    derivative in its own array first (the BL algorithm of §2.3.1).
+ *    stage update in the same kernel (the "store none" class of §2.3, with
+ *    the RK update of Fig. 1 fused in): the product path.  Variant
+ *    SBLI_STORE_ALL stores each derivative in its own array first (the BL
+ *    algorithm of §2.3).  Variants SBLI_RS and SBLI_SS store the 9 velocity
+ *    gradients to arrays and evaluate the other derivatives on the fly,
+ *    recomputed at each occurrence (RS) or once into thread-local variables
+ *    (SS); SBLI_RA, SBLI_SN and SBLI_SN2 store nothing and recompute every
+ *    derivative at each occurrence (RA), or evaluate each once into
+ *    thread-local variables in listed order (SN) or grouped by velocity
+ *    component (SN2): the paper's intermediate- and minimal-storage classes
+ *    (§2.3), one thread per point, binary64 only, for comparison.
  */
 #ifndef SBLI_H
 #define SBLI_H
@@ -63,8 +76,16 @@ enum sbli_status {
   SBLI_EUNSUPPORTED = 5  /* precision/variant combination not provided */
 };
 
-enum sbli_precision { SBLI_FP64 = 0, SBLI_FP32 = 1, SBLI_FP32_DF = 2 };
-enum sbli_variant { SBLI_FUSED = 0, SBLI_STORE_ALL = 1 };
+enum sbli_precision { SBLI_FP64 = 0, SBLI_FP32 = 1, SBLI_FP32_DF = 2, SBLI_DF64 = 3 };
+enum sbli_variant {
+  SBLI_FUSED = 0,
+  SBLI_STORE_ALL = 1,
+  SBLI_RS = 2,
+  SBLI_SS = 3,
+  SBLI_RA = 4,
+  SBLI_SN = 5,
+  SBLI_SN2 = 6
+};
 
 /* Physical parameters (§2 Eqs. 1-5, §4): Re may be +INFINITY, which removes
  * the viscous and heat-flux terms. */

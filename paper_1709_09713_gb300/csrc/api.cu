@@ -60,13 +60,16 @@ bool valid_sizes(int n0, int n1, int n2) {
 
 FusedConfig default_config(const Geom& g, int precision);
 
+// binary64 state, accumulator and stage registers (three-register rotation)
+bool f64_registers(int precision) { return precision == SBLI_FP64 || precision == SBLI_DF64; }
+
 Layout layout_for(int n0, int n1, int n2, int precision, int variant) {
   Geom g{n0, n1, n2, (long long)n0 * n1 * n2};
   Layout L{};
   L.reg64 = align_up((size_t)g.P * 5 * sizeof(double));
   L.reg32 = align_up((size_t)g.P * 5 * sizeof(float));
-  L.n64 = precision == SBLI_FP64 ? 3 : 2;
-  L.n32 = precision == SBLI_FP64 ? 0 : 2;
+  L.n64 = f64_registers(precision) ? 3 : 2;
+  L.n32 = f64_registers(precision) ? 0 : 2;
   // partial sums: the fused kernel's CTAs for any configuration the grid may
   // use (the smallest zc gives the most CTAs), or the KE kernel's blocks
   const long long tiles = (long long)((n0 + 31) / 32) * ((n1 + 3) / 4);
@@ -75,7 +78,7 @@ Layout layout_for(int n0, int n1, int n2, int precision, int variant) {
   L.partials = align_up((size_t)(2 * np + 2) * sizeof(double));
   L.storeall = variant == SBLI_STORE_ALL
                    ? align_up(storeall_scratch_doubles(g, precision == SBLI_FP64 ? 8 : 4) * sizeof(double))
-                   : 0;
+                   : align_up(algorithm_scratch_doubles(g, variant) * sizeof(double));
   L.total = L.reg64 * L.n64 + L.reg32 * L.n32 + L.partials + L.storeall;
   return L;
 }
@@ -106,6 +109,7 @@ struct sbli_grid {
   FusedConfig cfg;
   Coef<double> cd;
   Coef<float> cf;
+  Coef<dfloat> cw;
   RefState ref;
   // graph of GRAPH_STEPS steps per starting register rotation
   static constexpr int GRAPH_STEPS = 6;
@@ -116,7 +120,7 @@ struct sbli_grid {
 namespace {
 
 // CTAs per SM a tile height allows (shared memory bound).
-int ctas_per_sm(int precision, int ty) { return (precision == SBLI_FP64 || ty >= 16) ? 1 : 2; }
+int ctas_per_sm(int precision, int ty) { return (f64_registers(precision) || ty >= 16) ? 1 : 2; }
 
 // Planes per CTA ranked by a wave-balance model: cost = waves * (zc + 1.5),
 // the 4 warm-up planes of a z segment costing about 1.5 full planes.
@@ -163,7 +167,7 @@ FusedConfig default_config(const Geom& g, int precision) {
 
 bool valid_config(int precision, int ty, int zc, int zq = 0) {
   if (zc < 4 || zq < 0 || zq > 1) return false;
-  if (precision == SBLI_FP64) return ty == 8 && zq == 0;
+  if (f64_registers(precision)) return ty == 8 && zq == 0;
   return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
 }
 
@@ -181,7 +185,7 @@ struct StagePtrs {
 
 StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
   StagePtrs p{};
-  if (g->precision == SBLI_FP64) {
+  if (f64_registers(g->precision)) {
     double* S = g->reg64[state];
     double* A = g->reg64[(state + 1) % 3];
     double* B = g->reg64[(state + 2) % 3];
@@ -221,7 +225,7 @@ StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
   return p;
 }
 
-int next_state(const sbli_grid* g, int state) { return g->precision == SBLI_FP64 ? (state + 1) % 3 : 1 - state; }
+int next_state(const sbli_grid* g, int state) { return f64_registers(g->precision) ? (state + 1) % 3 : 1 - state; }
 
 // Enqueue stage k on stream s for the given rotation; ke_partials != nullptr
 // (stage 0 only) also accumulates the diagnostics of the stage input.
@@ -243,9 +247,14 @@ cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_
     a.dacc_in = p.dacc_in;
     a.dacc_out = p.dacc_out;
     if (g->precision == SBLI_FP64) return launch_fused_fp64(a, g->cd, g->cfg, false, s);
+    if (g->precision == SBLI_DF64) return launch_fused_df64(a, g->cw, g->cfg, false, s);
     if (g->precision == SBLI_FP32_DF) return launch_fused_fp32df(a, g->cf, g->cfg, false, s);
     return launch_fused_fp32(a, g->cf, g->cfg, p.in64, false, s);
   }
+  if (g->variant > SBLI_STORE_ALL)
+    return launch_algorithm_stage(g->variant, g->geom, g->cd, static_cast<const double*>(p.q_in), p.acc_in,
+                                  p.acc_out, static_cast<double*>(p.q_out), nullptr, a_dt, b_dt,
+                                  static_cast<double*>(g->storeall), s);
   // store-all: residual into scratch, then the update kernel
   cudaError_t e;
   if (g->precision == SBLI_FP64) {
@@ -316,11 +325,12 @@ const char* sbli_last_error(void) { return g_last_error.c_str(); }
 int sbli_workspace_bytes(int n0, int n1, int n2, int precision, int variant, size_t* bytes) {
   if (!bytes) return fail(SBLI_EINVAL, "bytes is null");
   if (!valid_sizes(n0, n1, n2)) return fail(SBLI_EINVAL, "grid %d x %d x %d: each edge must be >= 5 and n0*n1 < 2^31", n0, n1, n2);
-  if (precision != SBLI_FP64 && precision != SBLI_FP32 && precision != SBLI_FP32_DF)
-    return fail(SBLI_EINVAL, "unknown precision %d", precision);
-  if (variant != SBLI_FUSED && variant != SBLI_STORE_ALL) return fail(SBLI_EINVAL, "unknown variant %d", variant);
-  if (precision == SBLI_FP32_DF && variant != SBLI_FUSED)
-    return fail(SBLI_EUNSUPPORTED, "the double-float accumulator is provided for the fused variant only");
+  if (precision < SBLI_FP64 || precision > SBLI_DF64) return fail(SBLI_EINVAL, "unknown precision %d", precision);
+  if (variant < SBLI_FUSED || variant > SBLI_SN2) return fail(SBLI_EINVAL, "unknown variant %d", variant);
+  if ((precision == SBLI_FP32_DF || precision == SBLI_DF64) && variant != SBLI_FUSED)
+    return fail(SBLI_EUNSUPPORTED, "the double-float modes are provided for the fused variant only");
+  if (variant > SBLI_STORE_ALL && precision != SBLI_FP64)
+    return fail(SBLI_EUNSUPPORTED, "the RS/SS/RA/SN/SN2 comparison variants are binary64 only");
   *bytes = layout_for(n0, n1, n2, precision, variant).total;
   return SBLI_OK;
 }
@@ -371,6 +381,7 @@ int sbli_create_grid(sbli_grid** out, int n0, int n1, int n2, int precision, int
   g->cfg = default_config(g->geom, precision);
   g->cd = make_coef<double>(g->n, p);
   g->cf = make_coef<float>(g->n, p);
+  g->cw = make_coef<dfloat>(g->n, p);
   g->ref = make_ref(p);
   cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -460,7 +471,7 @@ int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host) 
   // convert through the binary64 register this stage does not read
   auto copy_out = [&](const void* src, bool src64, double* dst) -> int {
     double* tmp = nullptr;
-    if (g->precision == SBLI_FP64) {
+    if (f64_registers(g->precision)) {
       // the register not used by this stage holds nothing live
       for (int r = 0; r < 3; ++r)
         if (g->reg64[r] != p.q_in && g->reg64[r] != p.acc_in) tmp = g->reg64[r];
@@ -511,9 +522,16 @@ int sbli_rhs(sbli_grid* g, double* r_dev) {
     a.q_in = q;
     a.r_out = r_dev;
     cudaError_t e = g->precision == SBLI_FP64      ? launch_fused_fp64(a, g->cd, g->cfg, true, g->stream)
+                    : g->precision == SBLI_DF64    ? launch_fused_df64(a, g->cw, g->cfg, true, g->stream)
                     : g->precision == SBLI_FP32_DF ? launch_fused_fp32df(a, g->cf, g->cfg, true, g->stream)
                                                    : launch_fused_fp32(a, g->cf, g->cfg, true, true, g->stream);
     SBLI_TRY(e, "fused rhs launch");
+    return SBLI_OK;
+  }
+  if (g->variant > SBLI_STORE_ALL) {
+    SBLI_TRY(launch_algorithm_stage(g->variant, g->geom, g->cd, q, nullptr, nullptr, nullptr, r_dev, 0.0, 0.0,
+                                    static_cast<double*>(g->storeall), g->stream),
+             "rhs launch");
     return SBLI_OK;
   }
   if (g->precision == SBLI_FP64) {

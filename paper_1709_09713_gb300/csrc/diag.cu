@@ -27,6 +27,7 @@ Coef<T> make_coef(const int n[3], const sbli_params& p) {
 }
 template Coef<double> make_coef<double>(const int[3], const sbli_params&);
 template Coef<float> make_coef<float>(const int[3], const sbli_params&);
+template Coef<dfloat> make_coef<dfloat>(const int[3], const sbli_params&);
 
 RefState make_ref(const sbli_params& p) {
   RefState r;

@@ -1,0 +1,25 @@
+// fused_df64.cu -- the fused stage kernel with binary64 storage and
+// double-float arithmetic (dfloat.cuh): stage inputs are split into
+// hi + lo binary32 pairs when a plane enters the ring, every derivative and
+// the residual run on the binary32 pipe, and the Runge-Kutta update of the
+// binary64 registers is the binary64 FMA of the binary64 path.
+#include "fused_stage.cuh"
+
+namespace sbli {
+
+template <int TY>
+static cudaError_t dispatch_df64(const StageArgs& a, const Coef<dfloat>& c, bool rhs_only, cudaStream_t s) {
+  if (rhs_only) return launch_fused_t<dfloat, double, double, TY, true, false>(a, c, s);
+  if (a.ke_partials) return launch_fused_t<dfloat, double, double, TY, false, true>(a, c, s);
+  return launch_fused_t<dfloat, double, double, TY, false, false>(a, c, s);
+}
+
+cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
+                              cudaStream_t s) {
+  switch (cfg.ty) {
+    case 8: return dispatch_df64<8>(a, c, rhs_only, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sbli

@@ -34,6 +34,7 @@
 // only through the reference enthalpy term -H0 div u).
 #pragma once
 
+#include "dfloat.cuh"
 #include "fpconv.cuh"
 #include "sbli_internal.cuh"
 
@@ -64,6 +65,8 @@ template <>
 __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
 template <>
 __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ dfloat rcp_rn<dfloat>(dfloat x) { return dw_reciprocal(x); }
 
 // Record load/store with 8-byte (binary32: 40-byte records) or 16-byte
 // (binary64: 80-byte records) vector accesses; both strides are bank-conflict
@@ -95,6 +98,21 @@ __device__ __forceinline__ void store_rec(double* p, const double (&r)[NV]) {
   double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll
   for (int i = 0; i < NV / 2; ++i) q[i] = make_double2(r[2 * i], r[2 * i + 1]);
+}
+// double-float records: 80 bytes, two values per 16-byte access
+__device__ __forceinline__ void load_rec(const dfloat* p, dfloat (&r)[NV]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) {
+    const float4 v = q[i];
+    r[2 * i] = dfloat(v.x, v.y);
+    r[2 * i + 1] = dfloat(v.z, v.w);
+  }
+}
+__device__ __forceinline__ void store_rec(dfloat* p, const dfloat (&r)[NV]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) q[i] = make_float4(r[2 * i].hi, r[2 * i].lo, r[2 * i + 1].hi, r[2 * i + 1].lo);
 }
 
 // ---- tensor memory (TMEM) as a per-thread queue of x2-neighbour records.
@@ -141,6 +159,8 @@ __device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, float (&r)
 }
 __device__ __forceinline__ void tmem_load_rec(uint32_t, int, double (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const double (&)[NV]) {}
+__device__ __forceinline__ void tmem_load_rec(uint32_t, int, dfloat (&)[NV]) {}
+__device__ __forceinline__ void tmem_store_rec(uint32_t, int, const dfloat (&)[NV]) {}
 
 // Allocate / release the CTA's TMEM columns (warp 0), publishing the base
 // address through shared memory.  The column budget per SM (at most 256 with
@@ -184,6 +204,19 @@ template <>
 __device__ __forceinline__ float to_compute<float, double>(double v) {
   return narrow_f64_fast(v);
 }
+// binary64 -> double-float: hi = RN32(v), lo = RN32(v - hi); the narrowings
+// and the widening of hi are integer re-packings, the remainder one DADD
+// (exact: v - hi has at most 29 significant bits)
+template <>
+__device__ __forceinline__ dfloat to_compute<dfloat, double>(double v) {
+  const float hi = narrow_f64_fast(v);
+  return dfloat(hi, narrow_f64_fast(v - widen_f32_fast(hi)));
+}
+
+// A stage value in binary64 for the Runge-Kutta update.
+__device__ __forceinline__ double as_double(double x) { return x; }
+__device__ __forceinline__ double as_double(float x) { return widen_f32_fast(x); }
+__device__ __forceinline__ double as_double(dfloat x) { return widen_f32_fast(x.hi) + widen_f32_fast(x.lo); }
 
 // Accumulated terms of the residual at one point.  By linearity of D1 and
 // because the centre values u_j^c are constants over a stencil, the
@@ -551,10 +584,10 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       R[4] = T(-0.5) * (t.rE + Ec * div) - c.H0 * div + c.inv_re * (uvisc + diss) + c.kappa * lapT;
 
       if (valid_xy) {
-        if (RHS_ONLY) {
+        if constexpr (RHS_ONLY) {
 #pragma unroll
           for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o_own] = double(R[f]);
-        } else if (DF) {
+        } else if constexpr (DF) {
           // binary32 stage, double-float accumulator (hi + lo, binary32
           // each): acc' = acc + (b dt R) by an error-free two-sum of hi and
           // the increment, the error folded into lo and renormalised;
@@ -574,11 +607,12 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             a.dacc_out[(long long)(NF + f) * a.g.P + o_own] = lo3;
             if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(hi3 + fmaf(ambdt, r, lo3));
           }
-        } else if (sizeof(T) == 8) {
-          // binary64 stage: acc + b dt R and acc + a dt R, fused multiply-adds
+        } else if constexpr (sizeof(T) == 8) {
+          // binary64 (or double-float) stage: acc + b dt R and acc + a dt R,
+          // binary64 fused multiply-adds
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            const double r = double(R[f]);
+            const double r = as_double(R[f]);
             a.acc_out[(long long)f * a.g.P + o_own] = fma(a.b_dt, r, accv[f]);
             if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(fma(a.a_dt, r, accv[f]));
           }

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "../../include/sbli.h"
+#include "dfloat.cuh"
 
 namespace sbli {
 
@@ -91,6 +92,9 @@ cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const Fu
 // binary32 stage with a double-float accumulator (stage inputs are binary32)
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s);
+// binary64 storage, double-float arithmetic (fused_df64.cu)
+cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
+                              cudaStream_t s);
 // the same two binary32 paths with the TMEM z queue (fused_fp32_tmem.cu)
 cudaError_t launch_fused_fp32_tmem(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                                    bool df, bool rhs_only, cudaStream_t s);
@@ -128,6 +132,19 @@ cudaError_t launch_storeall_rhs_fp32(const Geom& g, const Coef<float>& c, const 
                                      float* scratch, float* r_out, cudaStream_t s);
 cudaError_t launch_rk_update(const Geom& g, const void* r, bool r_fp64, const double* acc_in, double* acc_out,
                              void* q_out, bool out_fp64, double a_dt, double b_dt, cudaStream_t s);
+// One derivative of one binary64 array (Eq. 6 for order 1, Eq. 7 for order 2)
+// along one axis into its own array, as the store-all variant computes them.
+cudaError_t launch_derivative_fp64(const Geom& g, const Coef<double>& c, const double* f, double* df, int axis,
+                                   int order, cudaStream_t s);
+
+// The paper's other evaluation strategies, binary64 (algorithms.cu): alg is
+// SBLI_RS, SBLI_SS, SBLI_RA, SBLI_SN or SBLI_SN2.  r_out != nullptr writes R
+// instead of the stage update.
+bool algorithm_stores_gradients(int alg);
+size_t algorithm_scratch_doubles(const Geom& g, int alg);
+cudaError_t launch_algorithm_stage(int alg, const Geom& g, const Coef<double>& c, const double* q_in,
+                                   const double* acc_in, double* acc_out, double* q_out, double* r_out, double a_dt,
+                                   double b_dt, double* scratch, cudaStream_t s);
 
 // Record msg as this host thread's sbli_last_error() and return code.
 int set_last_error(int code, const char* msg);

@@ -227,6 +227,11 @@ __global__ void rk_update_kernel(long long n, const TR* __restrict__ r, const do
 
 }  // namespace
 
+cudaError_t launch_derivative_fp64(const Geom& g, const Coef<double>& c, const double* f, double* df, int axis,
+                                   int order, cudaStream_t s) {
+  return launch_der<double, double>(g, c, f, df, axis, order, s);
+}
+
 size_t storeall_scratch_doubles(const Geom& g, int elem_bytes) {
   // A_COUNT arrays of the arithmetic type, plus (binary32 only) a binary32
   // copy of the 5 conserved fields for a binary64 stage-0 input.

@@ -68,7 +68,10 @@ def test_rejects_unknown_modes(sbli):
         sbli.sbli_workspace_bytes(8, 8, 8, 7, sbli.SBLI_FUSED)
     assert e.value.code == sbli.SBLI_EINVAL
     with pytest.raises(sbli.SbliError) as e:
-        sbli.sbli_workspace_bytes(8, 8, 8, sbli.SBLI_FP64, 9)
+        sbli.sbli_workspace_bytes(8, 8, 8, sbli.SBLI_FP64, 7)
+    assert e.value.code == sbli.SBLI_EINVAL
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(8, 8, 8, sbli.SBLI_FP64, -1)
     assert e.value.code == sbli.SBLI_EINVAL
 
 
@@ -80,6 +83,28 @@ def test_workspace_sizes(sbli):
     assert f64 >= 3 * 5 * P * 8 and f64 < 3 * 5 * P * 8 + (1 << 20)
     assert f32 >= 2 * 5 * P * 8 + 2 * 5 * P * 4
     assert bl >= f64 + 82 * P * 8
+    # intermediate storage: primitives (u_i, p, T) and the 9 velocity gradients
+    for v in (sbli.SBLI_RS, sbli.SBLI_SS):
+        assert sbli.sbli_workspace_bytes(32, 32, 32, sbli.SBLI_FP64, v) == f64 + 14 * P * 8
+    # minimal storage: the primitive arrays only, no derivative arrays
+    for v in (sbli.SBLI_RA, sbli.SBLI_SN, sbli.SBLI_SN2):
+        assert sbli.sbli_workspace_bytes(32, 32, 32, sbli.SBLI_FP64, v) == f64 + 5 * P * 8
+
+
+def test_df64_uses_the_binary64_registers(sbli):
+    f64 = sbli.sbli_workspace_bytes(24, 20, 16, sbli.SBLI_FP64, sbli.SBLI_FUSED)
+    assert sbli.sbli_workspace_bytes(24, 20, 16, sbli.SBLI_DF64, sbli.SBLI_FUSED) == f64
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(24, 20, 16, sbli.SBLI_DF64, sbli.SBLI_STORE_ALL)
+    assert e.value.code == sbli.SBLI_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5, 6])
+def test_comparison_variants_are_binary64_only(sbli, precision, variant):
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(16, 16, 16, precision, variant)
+    assert e.value.code == sbli.SBLI_EUNSUPPORTED
 
 
 def test_null_arguments_are_errors(sbli):

@@ -57,7 +57,10 @@ def to_dev(q):
 GRIDS = [(32, 32, 32), (40, 24, 20), (37, 11, 9), (5, 5, 5), (5, 6, 7), (64, 16, 8)]
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+ALL_VARIANTS = [0, 1, 2, 3, 4, 5, 6]  # fused, BL, RS, SS, RA, SN, SN2
+
+
+@pytest.mark.parametrize("variant", ALL_VARIANTS)
 @pytest.mark.parametrize("n", GRIDS)
 def test_rhs_fp64_matches_oracle(S, orc, n, variant):
     q = random_state(n, seed=sum(n))
@@ -66,6 +69,41 @@ def test_rhs_fp64_matches_oracle(S, orc, n, variant):
     r = g.rhs().cpu().numpy()
     want = orc.rhs(orc.params(n), q)
     errs = rel_fields(r, want)
+    assert max(errs) <= 1e-12, errs
+
+
+@pytest.mark.parametrize("n", GRIDS)
+def test_rhs_df64_matches_oracle(S, orc, n):
+    """Double-float stage arithmetic on binary64 registers: the residual to
+    the binary64 bar."""
+    q = random_state(n, seed=11 + sum(n))
+    g = S.Grid(n, S.SBLI_DF64, S.SBLI_FUSED)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    want = orc.rhs(orc.params(n), q)
+    errs = rel_fields(r, want)
+    print("df64 residual errors", errs)
+    assert max(errs) <= 1e-12, errs
+
+
+def test_tgv_32_df64_ten_steps_and_history(S, orc):
+    """The 32^3 Taylor-Green case with double-float stage arithmetic: state
+    after 10 steps and the kinetic-energy/enstrophy history against the
+    oracle, <= 1e-12."""
+    n, dt, steps = 32, 1e-3, 10
+    g = S.Grid(n, S.SBLI_DF64, S.SBLI_FUSED)
+    g.init_tgv(1.0)
+    hist = g.step_n_history(steps, dt).cpu().numpy()
+    got = g.get_state().cpu().numpy()
+    p = orc.params(n)
+    q = orc.init_tgv(p)
+    for s in range(steps):
+        ke_o, ens_o = orc.ke_enstrophy(p, q)
+        assert abs(hist[s, 0] - ke_o) / ke_o <= 1e-12
+        assert abs(hist[s, 1] - ens_o) / ens_o <= 1e-12
+        q = orc.step(p, q, dt, 1)
+    errs = rel_fields(got, q)
+    print("df64 state errors", errs)
     assert max(errs) <= 1e-12, errs
 
 
@@ -92,10 +130,11 @@ def test_init_tgv_matches_oracle(S, orc, precision):
         assert max(rel_fields(got, want)) <= 1e-14
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", ALL_VARIANTS)
 def test_tgv_32_fp64_ten_steps(S, orc, variant):
     """The 32^3 Taylor-Green case (Re 1600, M 0.1, dt 1e-3, 10 steps):
-    fused and store-all binary64 paths against the oracle, <= 1e-12."""
+    the fused path and every comparison algorithm (BL, RS, SS, RA, SN, SN2)
+    against the oracle, <= 1e-12."""
     n, dt, steps = 32, 1e-3, 10
     g = S.Grid(n, S.SBLI_FP64, variant)
     g.init_tgv(1.0)
