@@ -373,7 +373,7 @@ def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=N
     g = S.Grid(n, prec, var, stream=stream)
     with torch.cuda.stream(stream):
         g.init_tgv(1.0)
-    cfg = list(g.autotune(3)[:3]) if tune else (list(g.config()) if var == S.SBLI_FUSED else None)
+    cfg = list(g.autotune(3)[:4]) if tune else (list(g.config()) if var == S.SBLI_FUSED else None)
     with torch.cuda.stream(stream):
         g.step_n(warmup, dt)
     ms = time_steps(S, g, stream, steps, dt, ws)

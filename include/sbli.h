@@ -190,14 +190,19 @@ SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, in
                                          void* stream);
 
 /* Launch configuration of the fused kernel: in-plane tile height (the tile
- * is 32 x tile_y points; binary64 grids use 8, binary32 grids 8 or 16),
- * planes per CTA along x2 (>= 4) and, for the binary32 paths, where each
- * thread keeps its column's records of the five x2 planes (z_queue = 0: the
- * shared-memory ring; 1: a per-thread queue in Blackwell tensor memory).
- * set_config validates and applies it (cached step graphs are rebuilt); must
- * be called at a step boundary.  z_queue may be NULL in get_config. */
-SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue);
-SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue);
+ * is 32 x tile_y points per column a thread owns; binary64 grids use 8,
+ * binary32 grids 8 or 16), planes per CTA along x2 (>= 4) and, for the
+ * binary32 paths, where each thread keeps its column's records of the five
+ * x2 planes (z_queue = 0: the shared-memory ring; 1: a per-thread queue in
+ * Blackwell tensor memory) and how many columns each thread owns
+ * (columns_per_thread = 1, or 2: columns x and x + 32 of a 64 x 8 tile
+ * computed together; shared-memory ring only).  Every configuration gives
+ * bitwise the same state.  set_config validates and applies it (cached step
+ * graphs are rebuilt); must be called at a step boundary.  z_queue and
+ * columns_per_thread may be NULL in get_config. */
+SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue,
+                             int* columns_per_thread);
+SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue, int columns_per_thread);
 
 /* Autotuner: times candidate configurations (each allowed tile height and
  * z queue with the planes-per-CTA values a wave-balance model ranks best) on
@@ -206,7 +211,7 @@ SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z
  * scratch registers, keeps the fastest and returns it.  The state is not
  * changed.  Synchronises the grid's stream.  Fused variant only. */
 SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue,
-                           float* best_stage_ms);
+                           int* columns_per_thread, float* best_stage_ms);
 
 /* ---------------------------------------------------------------------
  * Batched ensembles: up to 64 members (each its own grid size, Re, M, Pr,

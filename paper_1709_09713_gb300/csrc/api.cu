@@ -120,15 +120,18 @@ struct sbli_grid {
 namespace {
 
 // CTAs per SM a tile height allows (shared memory bound).
-int ctas_per_sm(int precision, int ty) { return (f64_registers(precision) || ty >= 16) ? 1 : 2; }
+int ctas_per_sm(int precision, int ty, int px = 1) {
+  return (f64_registers(precision) || ty >= 16 || px == 2) ? 1 : 2;
+}
 
 // Planes per CTA ranked by a wave-balance model: cost = waves * (zc + 1.5),
 // the 4 warm-up planes of a z segment costing about 1.5 full planes.
-void rank_zc(const Geom& g, int precision, int ty, int* best, int nbest) {
+void rank_zc(const Geom& g, int precision, int ty, int* best, int nbest, int px = 1) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long slots = (long long)sms * ctas_per_sm(precision, ty);
-  const long long tiles = (long long)((g.n0 + 31) / 32) * ((g.n1 + ty - 1) / ty);
+  const long long slots = (long long)sms * ctas_per_sm(precision, ty, px);
+  const int w = 32 * px;
+  const long long tiles = (long long)((g.n0 + w - 1) / w) * ((g.n1 + ty - 1) / ty);
   double cost[8];
   for (int i = 0; i < nbest; ++i) {
     best[i] = 0;
@@ -159,15 +162,17 @@ FusedConfig default_config(const Geom& g, int precision) {
   FusedConfig cfg;
   cfg.ty = 8;
   cfg.zq = 0;
+  cfg.px = 1;
   int zc[1];
   rank_zc(g, precision, cfg.ty, zc, 1);
   cfg.zc = std::max(4, std::min(zc[0], g.n2));
   return cfg;
 }
 
-bool valid_config(int precision, int ty, int zc, int zq = 0) {
-  if (zc < 4 || zq < 0 || zq > 1) return false;
-  if (f64_registers(precision)) return ty == 8 && zq == 0;
+bool valid_config(int precision, int ty, int zc, int zq = 0, int px = 1) {
+  if (zc < 4 || zq < 0 || zq > 1 || px < 1 || px > 2) return false;
+  if (f64_registers(precision)) return ty == 8 && zq == 0 && px == 1;
+  if (px == 2) return ty == 8 && zq == 0;  // 64 x 8 two-column tiles, shared-memory ring
   return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
 }
 
@@ -626,51 +631,58 @@ int sbli_kinetic_energy(sbli_grid* g, double* ke, double* enstrophy) {
   return SBLI_OK;
 }
 
-int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue) {
+int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue, int* columns_per_thread) {
   if (!g || !tile_y || !planes_per_cta) return fail(SBLI_EINVAL, "null argument");
   *tile_y = g->cfg.ty;
   *planes_per_cta = g->cfg.zc;
   if (z_queue) *z_queue = g->cfg.zq;
+  if (columns_per_thread) *columns_per_thread = g->cfg.px;
   return SBLI_OK;
 }
 
-int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue) {
+int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue, int columns_per_thread) {
   if (int rc = check_grid(g)) return rc;
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "set_config between stages of a step");
-  if (!valid_config(g->precision, tile_y, planes_per_cta, z_queue) || (z_queue && g->variant != SBLI_FUSED))
-    return fail(SBLI_EINVAL, "config tile_y=%d planes_per_cta=%d z_queue=%d not available for this grid", tile_y,
-                planes_per_cta, z_queue);
+  if (!valid_config(g->precision, tile_y, planes_per_cta, z_queue, columns_per_thread) ||
+      ((z_queue || columns_per_thread != 1) && g->variant != SBLI_FUSED))
+    return fail(SBLI_EINVAL,
+                "config tile_y=%d planes_per_cta=%d z_queue=%d columns_per_thread=%d not available for this grid",
+                tile_y, planes_per_cta, z_queue, columns_per_thread);
   FusedConfig cfg;
   cfg.ty = tile_y;
   cfg.zc = std::min(planes_per_cta, g->geom.n2);
   cfg.zq = z_queue;
-  if (cfg.ty != g->cfg.ty || cfg.zc != g->cfg.zc || cfg.zq != g->cfg.zq) {
+  cfg.px = columns_per_thread;
+  if (cfg.ty != g->cfg.ty || cfg.zc != g->cfg.zc || cfg.zq != g->cfg.zq || cfg.px != g->cfg.px) {
     g->cfg = cfg;
     drop_graphs(g);
   }
   return SBLI_OK;
 }
 
-int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue, float* best_stage_ms) {
+int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue, int* columns_per_thread,
+                  float* best_stage_ms) {
   if (int rc = check_grid(g)) return rc;
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "autotune between stages of a step");
   if (g->variant != SBLI_FUSED) return fail(SBLI_EUNSUPPORTED, "autotune needs the fused variant");
   if (reps < 1) return fail(SBLI_EINVAL, "reps must be >= 1");
-  FusedConfig cand[16];
+  FusedConfig cand[24];
   int nc = 0;
   const int tys[2] = {8, 16};
-  for (int zq = 0; zq < 2; ++zq)
-    for (int t = 0; t < 2; ++t) {
-      if (!valid_config(g->precision, tys[t], 4, zq)) continue;
-      int zc[3];
-      rank_zc(g->geom, g->precision, tys[t], zc, 3);
-      for (int i = 0; i < 3; ++i) {
-        bool dup = false;
-        const int z = std::max(4, std::min(zc[i], g->geom.n2));
-        for (int j = 0; j < nc; ++j) dup |= (cand[j].ty == tys[t] && cand[j].zc == z && cand[j].zq == zq);
-        if (!dup && nc < 16) cand[nc++] = FusedConfig{tys[t], z, zq};
+  for (int px = 1; px <= 2; ++px)
+    for (int zq = 0; zq < 2; ++zq)
+      for (int t = 0; t < 2; ++t) {
+        if (!valid_config(g->precision, tys[t], 4, zq, px)) continue;
+        int zc[3];
+        rank_zc(g->geom, g->precision, tys[t], zc, 3, px);
+        for (int i = 0; i < 3; ++i) {
+          bool dup = false;
+          const int z = std::max(4, std::min(zc[i], g->geom.n2));
+          for (int j = 0; j < nc; ++j)
+            dup |= (cand[j].ty == tys[t] && cand[j].zc == z && cand[j].zq == zq && cand[j].px == px);
+          if (!dup && nc < 24) cand[nc++] = FusedConfig{tys[t], z, zq, px};
+        }
       }
-    }
   cudaEvent_t e0, e1;
   SBLI_TRY(cudaEventCreate(&e0), "cudaEventCreate");
   cudaError_t ce = cudaEventCreate(&e1);
@@ -705,10 +717,12 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int*
     return cuda_fail(err, "autotune launch");
   }
   g->cfg = cand[best];
-  if (g->cfg.ty != saved.ty || g->cfg.zc != saved.zc || g->cfg.zq != saved.zq) drop_graphs(g);
+  if (g->cfg.ty != saved.ty || g->cfg.zc != saved.zc || g->cfg.zq != saved.zq || g->cfg.px != saved.px)
+    drop_graphs(g);
   if (tile_y) *tile_y = g->cfg.ty;
   if (planes_per_cta) *planes_per_cta = g->cfg.zc;
   if (z_queue) *z_queue = g->cfg.zq;
+  if (columns_per_thread) *columns_per_thread = g->cfg.px;
   if (best_stage_ms) *best_stage_ms = best_ms;
   return SBLI_OK;
 }

@@ -22,6 +22,7 @@ static cudaError_t dispatch32(const StageArgs& a, const Coef<float>& c, bool in_
 
 cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                               bool rhs_only, cudaStream_t s) {
+  if (cfg.px == 2) return launch_fused_fp32_pair(a, c, cfg, in_fp64, false, rhs_only, s);
   if (cfg.zq) return launch_fused_fp32_tmem(a, c, cfg, in_fp64, false, rhs_only, s);
   switch (cfg.ty) {
     case 8: return dispatch32<8>(a, c, in_fp64, rhs_only, s);
@@ -39,6 +40,7 @@ static cudaError_t dispatch32df(const StageArgs& a, const Coef<float>& c, bool r
 
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s) {
+  if (cfg.px == 2) return launch_fused_fp32_pair(a, c, cfg, false, true, rhs_only, s);
   if (cfg.zq) return launch_fused_fp32_tmem(a, c, cfg, false, true, rhs_only, s);
   switch (cfg.ty) {
     case 8: return dispatch32df<8>(a, c, rhs_only, s);
@@ -48,7 +50,8 @@ cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const 
 }
 
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg) {
-  const long long gx = (g.n0 + TX - 1) / TX, gy = (g.n1 + cfg.ty - 1) / cfg.ty, gz = (g.n2 + cfg.zc - 1) / cfg.zc;
+  const long long w = TX * (cfg.px == 2 ? 2 : 1);
+  const long long gx = (g.n0 + w - 1) / w, gy = (g.n1 + cfg.ty - 1) / cfg.ty, gz = (g.n2 + cfg.zc - 1) / cfg.zc;
   return (int)(gx * gy * gz);
 }
 

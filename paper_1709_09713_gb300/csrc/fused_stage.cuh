@@ -34,7 +34,10 @@
 // only through the reference enthalpy term -H0 div u).
 #pragma once
 
+#include <type_traits>
+
 #include "dfloat.cuh"
+#include "f32x2.cuh"
 #include "fpconv.cuh"
 #include "sbli_internal.cuh"
 
@@ -67,6 +70,8 @@ template <>
 __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
 template <>
 __device__ __forceinline__ dfloat rcp_rn<dfloat>(dfloat x) { return dw_reciprocal(x); }
+template <>
+__device__ __forceinline__ f32x2 rcp_rn<f32x2>(f32x2 x) { return f32x2(__frcp_rn(x.x), __frcp_rn(x.y)); }
 
 // Record load/store with 8-byte (binary32: 40-byte records) or 16-byte
 // (binary64: 80-byte records) vector accesses; both strides are bank-conflict
@@ -98,6 +103,21 @@ __device__ __forceinline__ void store_rec(double* p, const double (&r)[NV]) {
   double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll
   for (int i = 0; i < NV / 2; ++i) q[i] = make_double2(r[2 * i], r[2 * i + 1]);
+}
+// two-column binary32 records: 80 bytes, two values of both columns per 16-byte access
+__device__ __forceinline__ void load_rec(const f32x2* p, f32x2 (&r)[NV]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) {
+    const float4 v = q[i];
+    r[2 * i] = f32x2(v.x, v.y);
+    r[2 * i + 1] = f32x2(v.z, v.w);
+  }
+}
+__device__ __forceinline__ void store_rec(f32x2* p, const f32x2 (&r)[NV]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < NV / 2; ++i) q[i] = make_float4(r[2 * i].x, r[2 * i].y, r[2 * i + 1].x, r[2 * i + 1].y);
 }
 // double-float records: 80 bytes, two values per 16-byte access
 __device__ __forceinline__ void load_rec(const dfloat* p, dfloat (&r)[NV]) {
@@ -161,6 +181,8 @@ __device__ __forceinline__ void tmem_load_rec(uint32_t, int, double (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const double (&)[NV]) {}
 __device__ __forceinline__ void tmem_load_rec(uint32_t, int, dfloat (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const dfloat (&)[NV]) {}
+__device__ __forceinline__ void tmem_load_rec(uint32_t, int, f32x2 (&)[NV]) {}
+__device__ __forceinline__ void tmem_store_rec(uint32_t, int, const f32x2 (&)[NV]) {}
 
 // Allocate / release the CTA's TMEM columns (warp 0), publishing the base
 // address through shared memory.  The column budget per SM (at most 256 with
@@ -213,6 +235,30 @@ __device__ __forceinline__ dfloat to_compute<dfloat, double>(double v) {
   return dfloat(hi, narrow_f64_fast(v - widen_f32_fast(hi)));
 }
 
+// a * b + c: left to the compiler's contraction for scalar types, an explicit
+// packed FMA for f32x2 (whose operators are not contracted)
+template <typename T>
+__device__ __forceinline__ T mad(T a, T b, T c) {
+  return a * b + c;
+}
+__device__ __forceinline__ f32x2 mad(f32x2 a, f32x2 b, f32x2 c) { return fma(a, b, c); }
+
+// A stage value built from the stage input of each column a thread owns.
+template <typename T, typename TIN>
+__device__ __forceinline__ T from_lanes(const TIN (&v)[1]) {
+  return to_compute<T, TIN>(v[0]);
+}
+template <typename T, typename TIN>
+__device__ __forceinline__ T from_lanes(const TIN (&v)[2]) {
+  return T(to_compute<float, TIN>(v[0]), to_compute<float, TIN>(v[1]));
+}
+
+// binary64-class arithmetic types (binary64 Runge-Kutta update in place)
+template <typename T>
+constexpr bool is_f64_class() {
+  return std::is_same<T, double>::value || std::is_same<T, dfloat>::value;
+}
+
 // A stage value in binary64 for the Runge-Kutta update.
 __device__ __forceinline__ double as_double(double x) { return x; }
 __device__ __forceinline__ double as_double(float x) { return widen_f32_fast(x); }
@@ -242,7 +288,8 @@ template <int A, typename T, typename LD, typename SF>
 __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
                                            Terms<T>& t) {
   const T c1 = c.c1[A], c2 = c.c2[A], e0 = c.e0[A], e1 = c.e1[A], e2 = c.e2[A];
-  auto d1 = [&](T fm2, T fm1, T fp1, T fp2) { return c1 * (fp1 - fm1) - c2 * (fp2 - fm2); };
+  const T nc2 = -c2;
+  auto d1 = [&](T fm2, T fm1, T fp1, T fp2) { return mad(c1, fp1 - fm1, nc2 * (fp2 - fm2)); };
 
   T r[4][NV];
 #pragma unroll
@@ -255,19 +302,21 @@ __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, cons
   // stencil weights times (u_A + u_A^c):  D1(f w) = f+1 W1 - f-1 V1 - f+2 W2 + f-2 V2
   const T W1 = c1 * (r[2][V_U0 + A] + ua), V1 = c1 * (r[1][V_U0 + A] + ua);
   const T W2 = c2 * (r[3][V_U0 + A] + ua), V2 = c2 * (r[0][V_U0 + A] + ua);
-  auto d1w = [&](int V) { return r[2][V] * W1 - r[1][V] * V1 - r[3][V] * W2 + r[0][V] * V2; };
+  const T nV1 = -V1, nW2 = -W2;
+  auto d1w = [&](int V) { return mad(r[0][V], V2, mad(r[3][V], nW2, mad(r[1][V], nV1, r[2][V] * W1))); };
   // stencil weights times u_A:  D1(f u_A)
   const T X1 = c1 * r[2][V_U0 + A], Y1 = c1 * r[1][V_U0 + A];
   const T X2 = c2 * r[3][V_U0 + A], Y2 = c2 * r[0][V_U0 + A];
+  const T mY1 = -Y1, mX2 = -X2;
 #pragma unroll
   for (int i = 0; i < 3; ++i) t.rM[i] += d1w(V_M0 + i);
-  t.rM[A] += T(2) * SBLI_D1(V_P);
-  t.rE += d1w(V_E) + T(2) * (r[2][V_P] * X1 - r[1][V_P] * Y1 - r[3][V_P] * X2 + r[0][V_P] * Y2);
+  t.rM[A] = mad(T(2), SBLI_D1(V_P), t.rM[A]);
+  t.rE += mad(T(2), mad(r[0][V_P], Y2, mad(r[3][V_P], mX2, mad(r[1][V_P], mY1, r[2][V_P] * X1))), d1w(V_E));
   t.rrho += d1(fma(ua, r[0][V_RHO], r[0][V_M0 + A]), fma(ua, r[1][V_RHO], r[1][V_M0 + A]),
                fma(ua, r[2][V_RHO], r[2][V_M0 + A]), fma(ua, r[3][V_RHO], r[3][V_M0 + A]));
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T off = e1 * (r[2][V_U0 + i] + r[1][V_U0 + i]) + e2 * (r[3][V_U0 + i] + r[0][V_U0 + i]);
+    const T off = mad(e1, r[2][V_U0 + i] + r[1][V_U0 + i], e2 * (r[3][V_U0 + i] + r[0][V_U0 + i]));
     t.lap[i] += off;
     if (i == A) {
       t.G[A] = fma(e0, uc[A], off) + d1(s[0], s[1], s[2], s[3]);
@@ -275,7 +324,7 @@ __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, cons
       t.g[i][A] = SBLI_D1(V_U0 + i);
     }
   }
-  t.lapT += e1 * (r[2][V_T] + r[1][V_T]) + e2 * (r[3][V_T] + r[0][V_T]);
+  t.lapT += mad(e1, r[2][V_T] + r[1][V_T], e2 * (r[3][V_T] + r[0][V_T]));
 #undef SBLI_D1
 }
 
@@ -286,6 +335,11 @@ __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, cons
 template <typename T, int TY>
 constexpr int fused_min_blocks() {
   return (sizeof(T) == 4 && TY <= 8) ? 2 : 1;
+}
+// tile width in points: 32 columns per warp row, times the columns per thread
+template <typename T>
+constexpr int tile_width() {
+  return TX * Lanes<T>::N;
 }
 
 // The z march of one CTA over the 32 x TY column tile (bx, by), output
@@ -305,15 +359,23 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   constexpr int NHALO = PTS - NT;                  // haloed points outside the tile
   constexpr int LPT = 1 + (NHALO + NT - 1) / NT;   // own point + halo points per thread
 
+  constexpr int PP = Lanes<T>::N;  // columns per thread: tx and tx + 32
   const int n0 = a.g.n0, n1 = a.g.n1, n2 = a.g.n2;
   const unsigned plane = (unsigned)n0 * (unsigned)n1;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int x0 = bx * TX, y0 = by * TY;
+  const int x0 = bx * (TX * PP), y0 = by * TY;
   const int zend = min(zend_req, n2);
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool valid_xy = (gx < n0) && (gy < n1);
-  const unsigned own_off = valid_xy ? (unsigned)gx + (unsigned)n0 * (unsigned)gy : 0u;
+  const int gy = y0 + ty;
+  bool valid[PP];
+  unsigned own[PP];
+#pragma unroll
+  for (int j = 0; j < PP; ++j) {
+    const int gx = x0 + tx + TX * j;
+    valid[j] = (gx < n0) && (gy < n1);
+    own[j] = valid[j] ? (unsigned)gx + (unsigned)n0 * (unsigned)gy : 0u;
+  }
+  const bool valid_xy = valid[0];  // column tx (the second column is valid only if the first is)
   // per-field base pointers; offsets inside a field are 32-bit (P < 2^32)
   const TIN* qf[NF];
   const double* accf[NF];
@@ -327,7 +389,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   // point first, then at most LPT-1 points of the halo ring (the two rows
   // above and below the tile at full haloed width, then the two columns on
   // each side of the tile rows)
-  int ld_off[LPT], ld_s[LPT];
+  int ld_off[LPT][PP], ld_s[LPT];
 #pragma unroll
   for (int l = 0; l < LPT; ++l) {
     int sy = -1, sx = -1;
@@ -348,10 +410,13 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       }
     }
     if (sy >= 0) {
-      ld_off[l] = wrapi(x0 - HALO + sx, n0) + n0 * wrapi(y0 - HALO + sy, n1);
+#pragma unroll
+      for (int j = 0; j < PP; ++j)
+        ld_off[l][j] = wrapi(x0 - HALO + sx + TX * j, n0) + n0 * wrapi(y0 - HALO + sy, n1);
       ld_s[l] = sy * SX + sx;
     } else {
-      ld_off[l] = -1;
+#pragma unroll
+      for (int j = 0; j < PP; ++j) ld_off[l][j] = -1;
       ld_s[l] = 0;
     }
   }
@@ -393,15 +458,18 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) rs[k] = (k + 1) % NSLOT;  // any permutation; warm-up fills all slots
 
-  TIN pf[LPT][NF];
+  TIN pf[LPT][NF][PP];
   auto issue_loads = [&](int it_load) {
     const unsigned zoff = (unsigned)wrapi(zbeg - HALO + it_load, n2) * plane;
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
-      if (ld_off[l] >= 0) {
-        const unsigned o = zoff + (unsigned)ld_off[l];
+      if (ld_off[l][0] >= 0) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) pf[l][f] = qf[f][o];
+        for (int j = 0; j < PP; ++j) {
+          const unsigned o = zoff + (unsigned)ld_off[l][j];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pf[l][f][j] = qf[f][o];
+        }
       }
     }
   };
@@ -422,18 +490,18 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       T* ring = &sm.ring[se][0][0][0];
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        if (l == 0 || ld_off[l] >= 0) {  // the own point is always loaded
+        if (l == 0 || ld_off[l][0] >= 0) {  // the own point is always loaded
           T rec[NV];
-          const T rho_p = to_compute<T, TIN>(pf[l][0]);
-          const T m0 = to_compute<T, TIN>(pf[l][1]);
-          const T m1 = to_compute<T, TIN>(pf[l][2]);
-          const T m2 = to_compute<T, TIN>(pf[l][3]);
-          const T E_p = to_compute<T, TIN>(pf[l][4]);
+          const T rho_p = from_lanes<T, TIN>(pf[l][0]);
+          const T m0 = from_lanes<T, TIN>(pf[l][1]);
+          const T m1 = from_lanes<T, TIN>(pf[l][2]);
+          const T m2 = from_lanes<T, TIN>(pf[l][3]);
+          const T E_p = from_lanes<T, TIN>(pf[l][4]);
           const T rinv = rcp_rn<T>(T(1) + rho_p);
           const T u0 = m0 * rinv, u1 = m1 * rinv, u2 = m2 * rinv;
-          const T mu = m0 * u0 + m1 * u1 + m2 * u2;
-          const T p_p = c.gm1 * (E_p - T(0.5) * mu);   // Eq. 4: p - p_ref
-          const T T_p = (c.gM2 * p_p - rho_p) * rinv;  // Eq. 5: T - 1
+          const T mu = mad(m2, u2, mad(m1, u1, m0 * u0));
+          const T p_p = c.gm1 * mad(T(-0.5), mu, E_p);    // Eq. 4: p - p_ref
+          const T T_p = mad(c.gM2, p_p, -rho_p) * rinv;  // Eq. 5: T - 1
           rec[V_RHO] = rho_p;
           rec[V_M0] = m0;
           rec[V_M1] = m1;
@@ -457,10 +525,10 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     {
       const T(*R)[SX][NV] = sm.ring[se];
       const int sy = ty + HALO, sx = tx + HALO;
-      const T d00 = c.c1[0] * (R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0]) -
-                    c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]);
-      const T d11 = c.c1[1] * (R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1]) -
-                    c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]);
+      const T d00 = mad(c.c1[0], R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0],
+                        -c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]));
+      const T d11 = mad(c.c1[1], R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1],
+                        -c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]));
       sm.dring[se][0][ty][tx] = d00;
       sm.dring[se][1][ty][tx] = d11;
     }
@@ -470,21 +538,27 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     // slot of plane zc + o, o = -2..2
     const int sl[5] = {rs[0], rs[1], rs[2], rs[3], rs[4]};
     const int scen = sl[2];
-    const unsigned o_own = (unsigned)zc * plane + own_off;
+    unsigned oc[PP];  // offsets of the thread's centre points
+#pragma unroll
+    for (int j = 0; j < PP; ++j) oc[j] = (unsigned)zc * plane + own[j];
 
-    // accumulator of the centre point, fetched before the arithmetic
-    double accv[NF];
-    float dhi[NF], dlo[NF];  // double-float accumulator (DF mode)
-    if (!RHS_ONLY && valid_xy) {
-      if (DF) {
+    // accumulator of the centre points, fetched before the arithmetic
+    double accv[NF][PP];
+    float dhi[NF][PP], dlo[NF][PP];  // double-float accumulator (DF mode)
+    if (!RHS_ONLY) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          dhi[f] = a.dacc_in[(long long)f * a.g.P + o_own];
-          dlo[f] = a.dacc_in[(long long)(NF + f) * a.g.P + o_own];
+      for (int j = 0; j < PP; ++j) {
+        if (!valid[j]) continue;
+        if (DF) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            dhi[f][j] = a.dacc_in[(long long)f * a.g.P + oc[j]];
+            dlo[f][j] = a.dacc_in[(long long)(NF + f) * a.g.P + oc[j]];
+          }
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) accv[f][j] = accf[f] ? accf[f][oc[j]] : double(qf[f][oc[j]]);
         }
-      } else {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) accv[f] = accf[f] ? accf[f][o_own] : double(qf[f][o_own]);
       }
     }
 
@@ -493,8 +567,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     {
       const int sy = ty + HALO, sx = tx + HALO;
       auto u2z = [&](int yy, int xx) {
-        return c.c1[2] * (sm.ring[sl[3]][yy][xx][V_U2] - sm.ring[sl[1]][yy][xx][V_U2]) -
-               c.c2[2] * (sm.ring[sl[4]][yy][xx][V_U2] - sm.ring[sl[0]][yy][xx][V_U2]);
+        return mad(c.c1[2], sm.ring[sl[3]][yy][xx][V_U2] - sm.ring[sl[1]][yy][xx][V_U2],
+                   -c.c2[2] * (sm.ring[sl[4]][yy][xx][V_U2] - sm.ring[sl[0]][yy][xx][V_U2]));
       };
       d22 = u2z(sy, sx);
       sm.s0buf[ty][sx] = sm.dring[scen][1][ty][tx] + d22;
@@ -504,12 +578,12 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       for (int j = 0; j < HPT; ++j) {
         const int hy = hxy[j] >> 8, hx = hxy[j] & 0xFF;
         if (hk[j] == 1) {
-          const T d11 = c.c1[1] * (R[hy + 1][hx][V_U1] - R[hy - 1][hx][V_U1]) -
-                        c.c2[1] * (R[hy + 2][hx][V_U1] - R[hy - 2][hx][V_U1]);
+          const T d11 = mad(c.c1[1], R[hy + 1][hx][V_U1] - R[hy - 1][hx][V_U1],
+                            -c.c2[1] * (R[hy + 2][hx][V_U1] - R[hy - 2][hx][V_U1]));
           (&sm.s0buf[0][0])[hdst[j]] = d11 + u2z(hy, hx);
         } else if (hk[j] == 2) {
-          const T d00 = c.c1[0] * (R[hy][hx + 1][V_U0] - R[hy][hx - 1][V_U0]) -
-                        c.c2[0] * (R[hy][hx + 2][V_U0] - R[hy][hx - 2][V_U0]);
+          const T d00 = mad(c.c1[0], R[hy][hx + 1][V_U0] - R[hy][hx - 1][V_U0],
+                            -c.c2[0] * (R[hy][hx + 2][V_U0] - R[hy][hx - 2][V_U0]));
           (&sm.s1buf[0][0])[hdst[j]] = d00 + u2z(hy, hx);
         }
       }
@@ -567,26 +641,29 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       const T div = t.g[0][0] + t.g[1][1] + t.g[2][2];
       const T rho = T(1) + rho_p;
       T R[5];
-      R[0] = T(-0.5) * (t.rrho + rho * div);
+      R[0] = T(-0.5) * mad(rho, div, t.rrho);
       T uvisc = T(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const T lap = fma(e0sum, uc[i], t.lap[i]);
-        const T visc = lap + t.G[i] * T(1.0 / 3.0);  // Laplacian + G - (2/3) G
-        uvisc += uc[i] * visc;
-        R[1 + i] = T(-0.5) * (t.rM[i] + mc[i] * div) + c.inv_re * visc;
+        const T visc = mad(t.G[i], T(1.0 / 3.0), lap);  // Laplacian + G - (2/3) G
+        uvisc = mad(uc[i], visc, uvisc);
+        R[1 + i] = mad(c.inv_re, visc, T(-0.5) * mad(mc[i], div, t.rM[i]));
       }
       // viscous dissipation du_i/dx_j (du_i/dx_j + du_j/dx_i - 2/3 div delta_ij)
       const T a01 = t.g[0][1] + t.g[1][0], a02 = t.g[0][2] + t.g[2][0], a12 = t.g[1][2] + t.g[2][1];
-      const T diss = T(2) * (t.g[0][0] * t.g[0][0] + t.g[1][1] * t.g[1][1] + t.g[2][2] * t.g[2][2]) + a01 * a01 +
-                     a02 * a02 + a12 * a12 - T(2.0 / 3.0) * div * div;
+      const T sq = mad(t.g[2][2], t.g[2][2], mad(t.g[1][1], t.g[1][1], t.g[0][0] * t.g[0][0]));
+      const T diss = mad(T(2), sq, mad(a12, a12, mad(a02, a02, mad(a01, a01, T(-2.0 / 3.0) * div * div))));
       const T lapT = fma(e0sum, Tc, t.lapT);
-      R[4] = T(-0.5) * (t.rE + Ec * div) - c.H0 * div + c.inv_re * (uvisc + diss) + c.kappa * lapT;
+      R[4] = mad(c.kappa, lapT, mad(c.inv_re, uvisc + diss, mad(-c.H0, div, T(-0.5) * mad(Ec, div, t.rE))));
 
-      if (valid_xy) {
+#pragma unroll
+      for (int j = 0; j < PP; ++j) {
+        if (!valid[j]) continue;
+        const unsigned o = oc[j];
         if constexpr (RHS_ONLY) {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o_own] = double(R[f]);
+          for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o] = double(lane(R[f], j));
         } else if constexpr (DF) {
           // binary32 stage, double-float accumulator (hi + lo, binary32
           // each): acc' = acc + (b dt R) by an error-free two-sum of hi and
@@ -595,26 +672,26 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           const float bdt = float(a.b_dt), ambdt = float(a.amb_dt);
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            const float r = float(R[f]);
+            const float r = float(lane(R[f], j));
             const float x = bdt * r;
-            const float s = __fadd_rn(dhi[f], x);
-            const float bb = __fsub_rn(s, dhi[f]);
-            const float err = __fadd_rn(__fsub_rn(dhi[f], __fsub_rn(s, bb)), __fsub_rn(x, bb));
-            const float lo2 = __fadd_rn(dlo[f], err);
+            const float s = __fadd_rn(dhi[f][j], x);
+            const float bb = __fsub_rn(s, dhi[f][j]);
+            const float err = __fadd_rn(__fsub_rn(dhi[f][j], __fsub_rn(s, bb)), __fsub_rn(x, bb));
+            const float lo2 = __fadd_rn(dlo[f][j], err);
             const float hi3 = __fadd_rn(s, lo2);
             const float lo3 = __fsub_rn(lo2, __fsub_rn(hi3, s));
-            a.dacc_out[(long long)f * a.g.P + o_own] = hi3;
-            a.dacc_out[(long long)(NF + f) * a.g.P + o_own] = lo3;
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(hi3 + fmaf(ambdt, r, lo3));
+            a.dacc_out[(long long)f * a.g.P + o] = hi3;
+            a.dacc_out[(long long)(NF + f) * a.g.P + o] = lo3;
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = TOUT(hi3 + fmaf(ambdt, r, lo3));
           }
-        } else if constexpr (sizeof(T) == 8) {
+        } else if constexpr (is_f64_class<T>()) {
           // binary64 (or double-float) stage: acc + b dt R and acc + a dt R,
           // binary64 fused multiply-adds
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const double r = as_double(R[f]);
-            a.acc_out[(long long)f * a.g.P + o_own] = fma(a.b_dt, r, accv[f]);
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(fma(a.a_dt, r, accv[f]));
+            a.acc_out[(long long)f * a.g.P + o] = fma(a.b_dt, r, accv[f][j]);
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = TOUT(fma(a.a_dt, r, accv[f][j]));
           }
         } else {
           // binary32 stage, binary64 accumulator: one DADD per field,
@@ -623,16 +700,18 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           const float bdt = float(a.b_dt), ambdt = float(a.amb_dt);
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            const float r = float(R[f]);
-            const double accn = accv[f] + widen_f32_fast(bdt * r);
-            a.acc_out[(long long)f * a.g.P + o_own] = accn;
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o_own] = TOUT(narrow_f64_fast(accn) + ambdt * r);
+            const float r = float(lane(R[f], j));
+            const double accn = accv[f][j] + widen_f32_fast(bdt * r);
+            a.acc_out[(long long)f * a.g.P + o] = accn;
+            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = TOUT(narrow_f64_fast(accn) + ambdt * r);
           }
         }
         if (WITH_KE) {
           const T w0 = t.g[2][1] - t.g[1][2], w1 = t.g[0][2] - t.g[2][0], w2 = t.g[1][0] - t.g[0][1];
-          ke_acc += double(T(0.5) * (mc[0] * uc[0] + mc[1] * uc[1] + mc[2] * uc[2]));
-          ens_acc += double(T(0.5) * rho * (w0 * w0 + w1 * w1 + w2 * w2));
+          const T ke_t = T(0.5) * (mc[0] * uc[0] + mc[1] * uc[1] + mc[2] * uc[2]);
+          const T ens_t = T(0.5) * rho * (w0 * w0 + w1 * w1 + w2 * w2);
+          ke_acc += double(lane(ke_t, j));
+          ens_acc += double(lane(ens_t, j));
         }
       }
     }
@@ -687,9 +766,9 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
   if (ZT) tmem_release<NCOL>(tbase);
 }
 
-template <int TY>
+template <int TY, int W = TX>
 inline dim3 fused_grid(const Geom& g, int zc) {
-  return dim3((g.n0 + TX - 1) / TX, (g.n1 + TY - 1) / TY, (g.n2 + zc - 1) / zc);
+  return dim3((g.n0 + W - 1) / W, (g.n1 + TY - 1) / TY, (g.n2 + zc - 1) / zc);
 }
 
 template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
@@ -703,7 +782,7 @@ cudaError_t launch_fused_t(const StageArgs& a, const Coef<T>& c, cudaStream_t s)
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k<<<fused_grid<TY>(a.g, a.zc), TX * TY, smem, s>>>(a, c);
+  k<<<fused_grid<TY, tile_width<T>()>(a.g, a.zc), TX * TY, smem, s>>>(a, c);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,8 @@ struct FusedConfig {
   int zc;  // planes per CTA
   int zq;  // binary32 paths: 0 = x2-neighbour records from the shared-memory
            // ring, 1 = from a per-thread queue in tensor memory (TMEM)
+  int px;  // binary32 paths: columns per thread (1, or 2 = columns x and x + 32
+           // of a 64 x ty tile computed together)
 };
 
 // Host launchers (defined in fused_fp64.cu / fused_fp32.cu).
@@ -95,6 +97,9 @@ cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const 
 // binary64 storage, double-float arithmetic (fused_df64.cu)
 cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
                               cudaStream_t s);
+// the two binary32 paths with two columns per thread (fused_fp32_pair.cu)
+cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
+                                   bool df, bool rhs_only, cudaStream_t s);
 // the same two binary32 paths with the TMEM z queue (fused_fp32_tmem.cu)
 cudaError_t launch_fused_fp32_tmem(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                                    bool df, bool rhs_only, cudaStream_t s);

@@ -67,10 +67,11 @@ SIGNATURES = {
     "sbli_kinetic_energy": (_c_int, [_vp, _DP, _DP]),
     "sbli_kinetic_energy_async": (_c_int, [_vp, _vp]),
     "sbli_kinetic_energy_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _vp]),
-    "sbli_get_config": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
-    "sbli_set_config": (_c_int, [_vp, _c_int, _c_int, _c_int]),
+    "sbli_get_config": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                 ctypes.POINTER(_c_int)]),
+    "sbli_set_config": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
     "sbli_autotune": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
-                               ctypes.POINTER(ctypes.c_float)]),
+                               ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
     "sbli_stage_count": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "sbli_batch_workspace_bytes": (_c_int, [_c_int, _vp, _c_int, ctypes.POINTER(_c_size_t)]),
     "sbli_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _vp, _vp, _c_int, _vp, _c_size_t, _vp]),
@@ -200,21 +201,21 @@ def sbli_kinetic_energy_noalloc(q_ptr: int, n0: int, n1: int, n2: int, L: float,
     _check(lib().sbli_kinetic_energy_noalloc(_vp(q_ptr), n0, n1, n2, float(L), _vp(out_ptr), _vp(stream)))
 
 
-def sbli_get_config(h: int) -> tuple[int, int, int]:
-    ty, zc, zq = _c_int(), _c_int(), _c_int()
-    _check(lib().sbli_get_config(_vp(h), ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(zq)))
-    return ty.value, zc.value, zq.value
+def sbli_get_config(h: int) -> tuple[int, int, int, int]:
+    ty, zc, zq, px = _c_int(), _c_int(), _c_int(), _c_int()
+    _check(lib().sbli_get_config(_vp(h), ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(zq), ctypes.byref(px)))
+    return ty.value, zc.value, zq.value, px.value
 
 
-def sbli_set_config(h: int, tile_y: int, planes_per_cta: int, z_queue: int = 0) -> None:
-    _check(lib().sbli_set_config(_vp(h), int(tile_y), int(planes_per_cta), int(z_queue)))
+def sbli_set_config(h: int, tile_y: int, planes_per_cta: int, z_queue: int = 0, columns_per_thread: int = 1) -> None:
+    _check(lib().sbli_set_config(_vp(h), int(tile_y), int(planes_per_cta), int(z_queue), int(columns_per_thread)))
 
 
-def sbli_autotune(h: int, reps: int = 3) -> tuple[int, int, int, float]:
-    ty, zc, zq, ms = _c_int(), _c_int(), _c_int(), ctypes.c_float()
+def sbli_autotune(h: int, reps: int = 3) -> tuple[int, int, int, int, float]:
+    ty, zc, zq, px, ms = _c_int(), _c_int(), _c_int(), _c_int(), ctypes.c_float()
     _check(lib().sbli_autotune(_vp(h), int(reps), ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(zq),
-                               ctypes.byref(ms)))
-    return ty.value, zc.value, zq.value, ms.value
+                               ctypes.byref(px), ctypes.byref(ms)))
+    return ty.value, zc.value, zq.value, px.value, ms.value
 
 
 def sbli_stage_count(h: int) -> int:
@@ -551,8 +552,8 @@ class Grid:
     def config(self):
         return sbli_get_config(self.handle)
 
-    def set_config(self, tile_y, planes_per_cta, z_queue=0):
-        sbli_set_config(self.handle, tile_y, planes_per_cta, z_queue)
+    def set_config(self, tile_y, planes_per_cta, z_queue=0, columns_per_thread=1):
+        sbli_set_config(self.handle, tile_y, planes_per_cta, z_queue, columns_per_thread)
 
     def autotune(self, reps=3):
         return sbli_autotune(self.handle, reps)

@@ -271,30 +271,62 @@ def test_error_paths_fault_nothing(S):
 @pytest.mark.parametrize(
     "precision,configs",
     [
-        (1, [(8, 4, 0), (8, 13, 0), (16, 7, 0), (16, 40, 0), (8, 13, 1), (16, 7, 1), (16, 40, 1), (8, 4, 1)]),
-        (2, [(8, 4, 0), (16, 7, 0), (8, 13, 1), (16, 40, 1)]),
-        (0, [(8, 4, 0), (8, 9, 0), (8, 40, 0)]),
+        (1, [(8, 4, 0, 1), (8, 13, 0, 1), (16, 7, 0, 1), (16, 40, 0, 1), (8, 13, 1, 1), (16, 7, 1, 1),
+             (16, 40, 1, 1), (8, 4, 1, 1), (8, 4, 0, 2), (8, 13, 0, 2), (8, 40, 0, 2)]),
+        (2, [(8, 4, 0, 1), (16, 7, 0, 1), (8, 13, 1, 1), (16, 40, 1, 1), (8, 5, 0, 2), (8, 40, 0, 2)]),
+        (0, [(8, 4, 0, 1), (8, 9, 0, 1), (8, 40, 0, 1)]),
+        (3, [(8, 4, 0, 1), (8, 40, 0, 1)]),
     ],
 )
-def test_launch_configs_are_bitwise_identical(S, precision, configs):
+@pytest.mark.parametrize("n", [(64, 48, 40), (96, 20, 12), (40, 9, 7)])
+def test_launch_configs_are_bitwise_identical(S, precision, configs, n):
     """Tile height, planes per CTA and where the x2-neighbour records live
     (shared-memory ring or TMEM queue) change only the work decomposition and
-    data movement: every point's arithmetic is the same, so the state is
-    bitwise equal."""
-    n, dt = (64, 48, 40), 1e-3
+    data movement: every point's arithmetic is the same, so the state (and
+    the kinetic-energy history up to the order of its sums) is bitwise equal.
+    Two columns per thread use packed two-lane instructions with their own
+    multiply-add fusion: bitwise equal among themselves, within the binary32
+    bar of the one-column kernels.  Grids with x0 extents that are not
+    multiples of 64 cover the two-column tiles' ragged edge."""
+    dt = 1e-3
     q = to_dev(random_state(n, 23))
-    ref = None
-    for ty, zc, zq in configs:
+    ref = {}
+    for ty, zc, zq, px in configs:
         g = S.Grid(n, precision, S.SBLI_FUSED)
-        g.set_config(ty, zc, zq)
-        assert g.config() == (ty, min(zc, n[2]), zq)
+        g.set_config(ty, zc, zq, px)
+        assert g.config() == (ty, min(zc, n[2]), zq, px)
         g.set_state(q)
         g.step_n(2, dt)
+        hist = g.step_n_history(2, dt).cpu().numpy()
         out = g.get_state()
-        if ref is None:
-            ref = out
+        if px not in ref:
+            ref[px] = (out, hist)
         else:
-            assert torch.equal(out, ref), (ty, zc)
+            assert torch.equal(out, ref[px][0]), (ty, zc, zq, px)
+            assert np.allclose(hist, ref[px][1], rtol=1e-13, atol=0), (ty, zc, zq, px)
+    if 2 in ref:
+        errs = rel_fields(ref[2][0].cpu().numpy(), ref[1][0].cpu().numpy())
+        assert max(errs) <= 1e-5, errs
+        assert np.allclose(ref[2][1], ref[1][1], rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("n", [(64, 32, 24), (96, 20, 12), (40, 9, 7)])
+def test_two_column_tiles_match_oracle(S, orc, precision, n):
+    """Two columns per thread (64 x 8 tiles, packed two-lane binary32
+    arithmetic) against the oracle: residual within the binary32 residual
+    bar, state after 5 steps within the binary32 state bar."""
+    q = random_state(n, seed=41 + sum(n))
+    g = S.Grid(n, precision, S.SBLI_FUSED)
+    g.set_config(8, 8, 0, 2)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    p = orc.params(n)
+    assert max(rel_fields(r, orc.rhs(p, q))) <= 1e-4
+    g.step_n(5, 1e-3)
+    got = g.get_state().cpu().numpy()
+    errs = rel_fields(got, orc.step(p, q, 1e-3, 5))
+    assert max(errs) <= 1e-5, errs
 
 
 def test_autotune_keeps_state_and_picks_a_valid_config(S):
@@ -302,10 +334,10 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     g = S.Grid(n, S.SBLI_FP32, S.SBLI_FUSED)
     g.init_tgv()
     before = g.get_state()
-    ty, zc, zq, ms = g.autotune(reps=2)
-    assert ty in (8, 16) and 4 <= zc <= n[2] and zq in (0, 1) and ms > 0
+    ty, zc, zq, px, ms = g.autotune(reps=2)
+    assert ty in (8, 16) and 4 <= zc <= n[2] and zq in (0, 1) and px in (1, 2) and ms > 0
     assert torch.equal(g.get_state(), before)
-    assert g.config() == (ty, zc, zq)
+    assert g.config() == (ty, zc, zq, px)
     g.step_n(1, 1e-3)
     with pytest.raises(S.SbliError):
         g.set_config(12, 8)
@@ -314,6 +346,12 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     d = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
     with pytest.raises(S.SbliError):
         d.set_config(8, 8, 1)  # the TMEM queue holds binary32 records only
+    with pytest.raises(S.SbliError):
+        d.set_config(8, 8, 0, 2)  # two columns per thread: binary32 only
+    with pytest.raises(S.SbliError):
+        g.set_config(16, 8, 0, 2)  # two-column tiles are 64 x 8
+    with pytest.raises(S.SbliError):
+        g.set_config(8, 8, 1, 2)  # ... with the shared-memory ring
 
 
 def test_fp32_kinetic_energy_history_512_subsample_bound(S, orc):
