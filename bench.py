@@ -52,13 +52,13 @@ ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "d
 # binary64 flop per point-stage the fused kernel executes (2 DFMA + DADD +
 # DMUL), counted by ncu on the 256^3 stage-1 launch (profiles/).
 FUSED_FP64_FLOP_PER_PT = 512.3
-# DRAM bytes per launch (stage-1 launch: 160 B/pt algorithmic) from the ncu
+# DRAM bytes per launch, mean over the three stages of a step, from the ncu
 # captures summarised in profiles/ (an entry is removed once its kernel changes)
-NCU_TRAFFIC = {("fp64", 256): 2.692e9}
+NCU_TRAFFIC = {("fp64", 256): 2.248e9}
 # thread instructions per point-stage of the double-float kernel (ncu,
 # smsp__inst_executed x 32 / points); its ceiling is one warp instruction per
 # clock per SM sub-partition
-DF64_INST_PER_PT = 5335.0
+DF64_INST_PER_PT = 5337.0
 
 
 def parse():
