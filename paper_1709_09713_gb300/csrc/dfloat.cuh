@@ -7,10 +7,10 @@
 // composed as in the double-word algorithms analysed by Joldes, Muller and
 // Popescu ("Tight and rigorous error bounds for basic building blocks of
 // double-word arithmetic", ACM TOMS 2017):
-//   add: the "sloppy" sum (2Sum of the high parts, low parts added, one
-//        Fast2Sum); its error is at most a few u^2 (|x| + |y|) with
-//        u = 2^-24, i.e. absolute in the operands' magnitude -- the same kind
-//        of bound a binary64 operation on rounded inputs has;
+//   add: the "sloppy" sum (2Sum of the high parts, low parts added); its
+//        error is at most a few u^2 (|x| + |y|) with u = 2^-24, i.e.
+//        absolute in the operands' magnitude -- the same kind of bound a
+//        binary64 operation on rounded inputs has;
 //   mul: the FMA product of the high parts with both cross terms folded into
 //        the error term (relative error a few u^2);
 //   reciprocal: one Newton step from the binary32 reciprocal.
@@ -48,12 +48,15 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 
 }  // namespace dw
 
+// Sums and products are left unnormalised (|lo| may exceed half an ulp of
+// hi by a few units): the next operation's 2Sum of the high parts and its
+// FMA error terms take any hi/lo split, so the renormalising Fast2Sum is
+// needed only where a value leaves the double-word form (dw_normalise).
+// The error bound stays a few u^2 times the operands' magnitudes.
 __device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
-  float sh, sl, zh, zl;
+  float sh, sl;
   dw::two_sum(x.hi, y.hi, sh, sl);
-  const float w = __fadd_rn(sl, __fadd_rn(x.lo, y.lo));
-  dw::fast_two_sum(sh, w, zh, zl);
-  return dfloat(zh, zl);
+  return dfloat(sh, __fadd_rn(sl, __fadd_rn(x.lo, y.lo)));
 }
 __device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
@@ -63,8 +66,11 @@ __device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
   float e = __fmaf_rn(x.hi, y.hi, -p);
   e = __fmaf_rn(x.hi, y.lo, e);
   e = __fmaf_rn(x.lo, y.hi, e);
+  return dfloat(p, e);
+}
+__device__ __forceinline__ dfloat dw_normalise(dfloat x) {
   float zh, zl;
-  dw::fast_two_sum(p, e, zh, zl);
+  dw::fast_two_sum(x.hi, x.lo, zh, zl);
   return dfloat(zh, zl);
 }
 // x * y + z.  The binary32 and binary64 overloads keep unqualified fma()
@@ -79,7 +85,8 @@ __device__ __forceinline__ dfloat& operator*=(dfloat& x, dfloat y) { return x = 
 
 // 1 / x: t = RN(1/x.hi), residual e = 1 - x t (FMA for the high part, the low
 // part subtracted), result t + t e.
-__device__ __forceinline__ dfloat dw_reciprocal(dfloat x) {
+__device__ __forceinline__ dfloat dw_reciprocal(dfloat xin) {
+  const dfloat x = dw_normalise(xin);
   const float t = __frcp_rn(x.hi);
   float e = __fmaf_rn(-x.hi, t, 1.0f);
   e = __fmaf_rn(-x.lo, t, e);
