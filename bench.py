@@ -313,10 +313,12 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709):
             "stage_ms": ms / (3 * steps), "launches_per_stage": 1}
 
 
-def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, arena_gb=200.0):
+def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, arena_gb=200.0, fp64_as=0):
     """Poisson arrivals of TGV solve requests (grid edge log-uniform, step
     count uniform, FP64/FP32 flag 50/50) replayed in wall-clock time against
-    the continuous-batching server; latency = completion - arrival."""
+    the continuous-batching server; latency = completion - arrival.
+    fp64_as: the precision FP64-flagged requests run in (SBLI_FP64, or
+    SBLI_DF64: the same 1e-12 bar in double-float arithmetic)."""
     import torch
 
     from paper_1709_09713_gb300 import workloads
@@ -332,7 +334,8 @@ def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, aren
         now = time.perf_counter() - t0
         while nxt < count and trace[nxt].arrival_s <= now:
             q = trace[nxt]
-            rid = srv.submit(S.request(q.n, q.precision, q.steps, 1e-3, Re=q.Re, Mach=q.Mach, amplitude=q.amplitude))
+            prec = fp64_as if q.precision == S.SBLI_FP64 else q.precision
+            rid = srv.submit(S.request(q.n, prec, q.steps, 1e-3, Re=q.Re, Mach=q.Mach, amplitude=q.amplitude))
             arrival[rid] = q.arrival_s
             nxt += 1
         st = srv.stats()
@@ -352,8 +355,9 @@ def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, aren
     def pct(p):
         return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
 
+    f64 = "fp64" if fp64_as == S.SBLI_FP64 else "fp64 (double-float arithmetic)"
     return {"workload": f"serving: {count} Poisson requests at {rate_hz} req/s, N log-uniform [{nmin},{nmax}], "
-                        f"steps U{{{steps_lo}..{steps_hi}}}, fp64/fp32 50/50, dt 1e-3",
+                        f"steps U{{{steps_lo}..{steps_hi}}}, {f64}/fp32 50/50, dt 1e-3",
             "value": work / wall, "unit": "pt-stage/s", "requests": count, "wall_s": wall,
             "p50_latency_s": pct(50), "p99_latency_s": pct(99), "max_latency_s": lat[-1],
             "offered_pt_stage_per_s": sum(3.0 * q.n**3 * q.steps for q in trace) / max(trace[-1].arrival_s, 1e-9)}
@@ -551,7 +555,9 @@ def run_ours(args):
                         leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
                         algorithms_leg(S, 256, args.alg_steps, 1, dt, ws, nvml),
                         ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws),
-                        serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi)]
+                        serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi),
+                        serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
+                                    fp64_as=S.SBLI_DF64)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_n, args.cpu_sample_steps, dt)
     if rank == 0:

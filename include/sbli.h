@@ -204,12 +204,12 @@ SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_ct
                              int* columns_per_thread);
 SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue, int columns_per_thread);
 
-/* Autotuner: times candidate configurations (each allowed tile height and
- * z queue with the planes-per-CTA values a wave-balance model ranks best) on
- * this grid with
- * `reps` timed stage-0 launches each, which read the state and write only the
- * scratch registers, keeps the fastest and returns it.  The state is not
- * changed.  Synchronises the grid's stream.  Fused variant only. */
+/* Autotuner: times candidate configurations (each allowed tile height, z
+ * queue and columns per thread with the planes-per-CTA values a wave-balance
+ * model ranks best) on this grid with `reps` timed stage-0 launches each,
+ * which read the state and write only the scratch registers, keeps the
+ * fastest and returns it.  The state is not changed.  Synchronises the grid's
+ * stream.  Fused variant only. */
 SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue,
                            int* columns_per_thread, float* best_stage_ms);
 
@@ -217,8 +217,9 @@ SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_
  * Batched ensembles: up to 64 members (each its own grid size, Re, M, Pr,
  * gamma, L) advanced together.  Every Runge-Kutta stage of all members is one
  * persistent kernel launch that walks the members' work items (z chunk x
- * 32 x 8 tile); step loops are captured as CUDA graphs.  Precision as for
- * single grids.  Members' results are bitwise those of the same member run
+ * 32 x 8 tile); step loops are captured as CUDA graphs.  Precision
+ * SBLI_FP64, SBLI_FP32 or SBLI_DF64, as for single grids (others:
+ * SBLI_EINVAL).  Members' results are bitwise those of the same member run
  * alone as a single grid with tile height 8.
  * n: 3*count edge lengths (n0, n1, n2 per member); params: count entries.
  * --------------------------------------------------------------------- */
@@ -262,7 +263,7 @@ typedef struct sbli_server sbli_server;
 
 typedef struct {
   int n0, n1, n2;      /* grid */
-  int precision;       /* SBLI_FP64 or SBLI_FP32 */
+  int precision;       /* SBLI_FP64, SBLI_FP32 or SBLI_DF64 */
   int steps;           /* time steps to run (>= 0) */
   double dt;           /* time step (> 0) */
   sbli_params params;  /* Re, M, Pr, gamma, L */

@@ -90,6 +90,23 @@ cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int gr
 }
 
 template <>
+cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(FusedSmem<dfloat, 8>);
+  static bool cfg = false;
+  if (!cfg) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<dfloat, double, double, 8, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<dfloat, double, double, 8, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    cfg = true;
+  }
+  if (p.ke_items) batch_stage_kernel<dfloat, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
+  else batch_stage_kernel<dfloat, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <>
 cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s) {
   const size_t smem = sizeof(FusedSmem<double, 8>);
   static bool cfg = false;
@@ -156,6 +173,10 @@ struct BatchLayout {
 };
 
 
+// binary64 registers with the three-register rotation (binary64 and
+// double-float arithmetic)
+bool batch_f64_registers(int precision) { return precision == SBLI_FP64 || precision == SBLI_DF64; }
+
 BatchLayout batch_layout(int count, const int* n, int precision) {
   BatchLayout L;
   L.m.resize(count);
@@ -172,9 +193,9 @@ BatchLayout batch_layout(int count, const int* n, int precision) {
     L.total_items += member_items(M.n);
   }
   L.reg64 = o64;
-  L.reg32 = precision == SBLI_FP64 ? 0 : o32;
-  L.n64 = precision == SBLI_FP64 ? 3 : 2;
-  L.n32 = precision == SBLI_FP64 ? 0 : 2;
+  L.reg32 = batch_f64_registers(precision) ? 0 : o32;
+  L.n64 = batch_f64_registers(precision) ? 3 : 2;
+  L.n32 = batch_f64_registers(precision) ? 0 : 2;
   L.items_bytes = balign((size_t)(2 * L.total_items + 2) * sizeof(double));
   // per member: KE result pair, 1/P, item begin; plus the KE kernel partials
   L.misc_bytes = balign((size_t)count * 2 * sizeof(double)) + balign((size_t)count * sizeof(double)) +
@@ -208,7 +229,7 @@ struct sbli_batch {
 
 namespace {
 
-int batch_next_state(const sbli_batch* b, int s) { return b->precision == SBLI_FP64 ? (s + 1) % 3 : 1 - s; }
+int batch_next_state(const sbli_batch* b, int s) { return batch_f64_registers(b->precision) ? (s + 1) % 3 : 1 - s; }
 
 Geom member_geom(const MemberLayout& M) { return Geom{M.n[0], M.n[1], M.n[2], M.P}; }
 
@@ -223,7 +244,7 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
   a.amb_dt = (RK_A[k] - RK_B[k]) * dt;
   auto r64 = [&](int r) { return reinterpret_cast<double*>(b->reg64[r] + M.off64); };
   auto r32 = [&](int r) { return reinterpret_cast<float*>(b->reg32[r] + M.off32); };
-  if (b->precision == SBLI_FP64) {
+  if (batch_f64_registers(b->precision)) {
     double* S = r64(state);
     double* A = r64((state + 1) % 3);
     double* B = r64((state + 2) % 3);
@@ -264,8 +285,9 @@ cudaError_t enqueue_batch_stage_t(sbli_batch* b, int k, int state, double dt, do
 }
 
 cudaError_t enqueue_batch_stage(sbli_batch* b, int k, int state, double dt, double* ke_items, cudaStream_t s) {
-  return b->precision == SBLI_FP64 ? enqueue_batch_stage_t<double>(b, k, state, dt, ke_items, s)
-                                   : enqueue_batch_stage_t<float>(b, k, state, dt, ke_items, s);
+  if (b->precision == SBLI_FP64) return enqueue_batch_stage_t<double>(b, k, state, dt, ke_items, s);
+  if (b->precision == SBLI_DF64) return enqueue_batch_stage_t<dfloat>(b, k, state, dt, ke_items, s);
+  return enqueue_batch_stage_t<float>(b, k, state, dt, ke_items, s);
 }
 
 void batch_drop_graphs(sbli_batch* b) {
@@ -317,7 +339,8 @@ extern "C" {
 int sbli_batch_workspace_bytes(int count, const int* n, int precision, size_t* bytes) {
   if (!bytes || !n) return bfail(SBLI_EINVAL, "null argument");
   if (count < 1 || count > BATCH_MAX_MEMBERS) return bfail(SBLI_EINVAL, "count %d not in 1..%d", count, BATCH_MAX_MEMBERS);
-  if (precision != SBLI_FP64 && precision != SBLI_FP32) return bfail(SBLI_EINVAL, "unknown precision %d", precision);
+  if (precision != SBLI_FP64 && precision != SBLI_FP32 && precision != SBLI_DF64)
+    return bfail(SBLI_EINVAL, "precision %d not available for batches (binary64, binary32, double-float)", precision);
   for (int i = 0; i < count; ++i) {
     const int* m = n + 3 * i;
     if (m[0] < 5 || m[1] < 5 || m[2] < 5 || (long long)m[0] * m[1] >= (1LL << 31) ||
@@ -372,7 +395,7 @@ int sbli_batch_create(sbli_batch** out, int count, const int* n, const sbli_para
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->grid_ctas = sms * (precision == SBLI_FP64 ? 1 : 2);
+  b->grid_ctas = sms * (batch_f64_registers(precision) ? 1 : 2);
   // per-member constants for the KE finalisation
   std::vector<double> inv(count);
   std::vector<long long> beg(count + 1);

@@ -108,11 +108,15 @@ struct Req {
   double ke = 0, ens = 0;
 };
 
+// binary64 registers with the three-register rotation (binary64 and
+// double-float arithmetic)
+bool req_f64_registers(int precision) { return precision == SBLI_FP64 || precision == SBLI_DF64; }
+
 size_t request_bytes(const sbli_request& r, size_t* reg64, size_t* reg32) {
   const long long P = (long long)r.n0 * r.n1 * r.n2;
   *reg64 = salign((size_t)P * 5 * sizeof(double));
   *reg32 = salign((size_t)P * 5 * sizeof(float));
-  return r.precision == SBLI_FP64 ? 3 * *reg64 : 2 * *reg64 + 2 * *reg32;
+  return req_f64_registers(r.precision) ? 3 * *reg64 : 2 * *reg64 + 2 * *reg32;
 }
 
 }  // namespace
@@ -153,7 +157,7 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
   a.b_dt = RK_B[k] * q.r.dt;
   a.amb_dt = (RK_A[k] - RK_B[k]) * q.r.dt;
   const int st = q.state;
-  if (q.r.precision == SBLI_FP64) {
+  if (req_f64_registers(q.r.precision)) {
     double* S = r64(s, q, st);
     double* A = r64(s, q, (st + 1) % 3);
     double* B = r64(s, q, (st + 2) % 3);
@@ -208,7 +212,8 @@ int valid_request(const sbli_request* r) {
   if (r->n0 < 5 || r->n1 < 5 || r->n2 < 5 || (long long)r->n0 * r->n1 >= (1LL << 31) ||
       (long long)r->n0 * r->n1 * r->n2 >= (1LL << 32))
     return sfail(SBLI_EINVAL, "request grid %d x %d x %d invalid", r->n0, r->n1, r->n2);
-  if (r->precision != SBLI_FP64 && r->precision != SBLI_FP32) return sfail(SBLI_EINVAL, "unknown precision");
+  if (r->precision != SBLI_FP64 && r->precision != SBLI_FP32 && r->precision != SBLI_DF64)
+    return sfail(SBLI_EINVAL, "precision %d not available for requests (binary64, binary32, double-float)", r->precision);
   if (r->steps < 0) return sfail(SBLI_EINVAL, "steps < 0");
   if (!(r->dt > 0) || !isfinite(r->dt)) return sfail(SBLI_EINVAL, "dt must be finite and > 0");
   const sbli_params& p = r->params;
@@ -220,7 +225,7 @@ int valid_request(const sbli_request* r) {
 
 // Final diagnostics and copy-out of a finished request; frees its block.
 int retire(sbli_server* s, Req& q) {
-  cudaStream_t st = q.r.precision == SBLI_FP64 ? s->s64 : s->s32;
+  cudaStream_t st = req_f64_registers(q.r.precision) ? s->s64 : s->s32;
   const Geom g{q.r.n0, q.r.n1, q.r.n2, q.P};
   const int n[3] = {q.r.n0, q.r.n1, q.r.n2};
   const double* state = r64(s, q, q.state);
@@ -329,17 +334,18 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     q.t_admit = s->now();
     q.state = 0;
     q.remaining = q.r.steps;
-    cudaStream_t st = q.r.precision == SBLI_FP64 ? s->s64 : s->s32;
+    cudaStream_t st = req_f64_registers(q.r.precision) ? s->s64 : s->s32;
     SBLI_STRY(launch_init_tgv(Geom{q.r.n0, q.r.n1, q.r.n2, q.P}, q.r.params, q.r.amplitude, r64(s, q, 0), st),
               "init_tgv");
     s->active.push_back(q);
   }
   // one time step for every active request with steps left
-  bool any64 = false, any32 = false;
+  bool any64 = false, any32 = false, anydw = false;
   for (const Req& q : s->active) {
-    if (q.remaining > 0) (q.r.precision == SBLI_FP64 ? any64 : any32) = true;
+    if (q.remaining > 0)
+      (q.r.precision == SBLI_FP64 ? any64 : q.r.precision == SBLI_DF64 ? anydw : any32) = true;
   }
-  if (any64 || any32) {
+  if (any64 || any32 || anydw) {
     // requests with no steps left sit out this step
     std::vector<Req> idle;
     for (auto it = s->active.begin(); it != s->active.end();) {
@@ -352,10 +358,11 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     }
     for (int k = 0; k < 3; ++k) {
       if (any64) SBLI_STRY(launch_group<double>(s, k, SBLI_FP64, s->s64, s->grid64), "fp64 stage");
+      if (anydw) SBLI_STRY(launch_group<dfloat>(s, k, SBLI_DF64, s->s64, s->grid64), "double-float stage");
       if (any32) SBLI_STRY(launch_group<float>(s, k, SBLI_FP32, s->s32, s->grid32), "fp32 stage");
     }
     for (Req& q : s->active) {
-      q.state = q.r.precision == SBLI_FP64 ? (q.state + 1) % 3 : 1 - q.state;
+      q.state = req_f64_registers(q.r.precision) ? (q.state + 1) % 3 : 1 - q.state;
       q.remaining--;
     }
     s->active.insert(s->active.end(), idle.begin(), idle.end());

@@ -30,7 +30,7 @@ MACH = [0.1, 0.25, 0.4, 0.15, 0.3]
 AMP = [1.0, 0.95, 1.08, 0.9, 1.02]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 3])
 def test_batch_members_equal_single_grids_bitwise(S, precision):
     dt, steps = 1e-3, 7  # one captured 6-step graph plus one direct step
     b = S.Batch(SIZES, precision, Re=RE, Mach=MACH)
@@ -44,9 +44,11 @@ def test_batch_members_equal_single_grids_bitwise(S, precision):
         assert torch.equal(b.get_state(m), g.get_state()), m
 
 
-def test_batch_matches_oracle_fp64(S, orc):
+@pytest.mark.parametrize("precision", [0, 3])
+def test_batch_matches_oracle_fp64(S, orc, precision):
+    """binary64 and double-float arithmetic members against the oracle."""
     dt, steps = 1e-3, 3
-    b = S.Batch(SIZES[:3], 0, Re=RE[:3], Mach=MACH[:3])
+    b = S.Batch(SIZES[:3], precision, Re=RE[:3], Mach=MACH[:3])
     b.init_tgv(AMP[:3])
     b.step_n(steps, dt)
     for m, n in enumerate(SIZES[:3]):

@@ -30,6 +30,8 @@ REQS = [  # n, precision, steps, Re, Mach, amplitude, submit at tick
     ((5, 6, 7), 1, 6, 50.0, 0.4, 1.1, 3),
     ((36, 36, 36), 1, 2, 1600.0, 0.1, 1.0, 5),
     ((16, 16, 16), 0, 0, 1600.0, 0.1, 1.0, 6),
+    ((24, 20, 16), 3, 6, 1600.0, 0.1, 1.0, 1),  # double-float arithmetic
+    ((32, 16, 12), 3, 3, 300.0, 0.2, 0.97, 4),
 ]
 
 
