@@ -480,3 +480,33 @@ def test_stage_chain_equals_rk_driver_bitwise(orc):
         q, acc = orc.stage(p, k, 2e-3, q, acc)
     assert np.array_equal(acc, orc.step(p, q0, 2e-3, 1))
     assert np.array_equal(q, acc)
+
+
+def test_oracle_matches_its_golden_fixture(orc):
+    """The oracle's 32^3 Taylor-Green history and sampled final state against
+    tests/golden/tgv32_oracle.txt (written by tests/golden/make_golden.py from
+    the oracle alone): guards the oracle's arithmetic against silent change.
+    Tolerance 1e-13: the fixture holds exact decimal reprs, the only freedom is
+    the thread partition of the oracle's compensated sums."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tgv32_oracle.txt")
+    hist, pts = [], []
+    for line in open(path):
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        if tok[0] == "h":
+            hist.append((float(tok[2]), float(tok[3])))
+        elif tok[0] == "q":
+            pts.append(((int(tok[1]), int(tok[2]), int(tok[3])), [float(x) for x in tok[4:9]]))
+    assert len(hist) == 10 and len(pts) == 6
+    p = orc.params(32)
+    q = orc.init_tgv(p)
+    for s in range(10):
+        ke, ens = orc.ke_enstrophy(p, q)
+        assert ke == pytest.approx(hist[s][0], rel=1e-13) and ens == pytest.approx(hist[s][1], rel=1e-13)
+        q = orc.step(p, q, 1e-3, 1)
+    for (i, j, k), want in pts:
+        for f in range(5):
+            assert q[f, k, j, i] == pytest.approx(want[f], rel=1e-13, abs=1e-15)
