@@ -38,17 +38,17 @@
  *    reference state (rho = 1, u = 0, p = 1/(gamma M^2)); the
  *    get/set calls convert to and from the plain conserved variables.
  *  - Variant SBLI_FUSED evaluates every derivative on the fly and writes the
- *    stage update in the same kernel (the "store none" class of §2.3, with
+ *    stage update in the same kernel (the minimal-storage class of §2.5, with
  *    the RK update of Fig. 1 fused in): the product path.  Variant
  *    SBLI_STORE_ALL stores each derivative in its own array first (the BL
- *    algorithm of §2.3).  Variants SBLI_RS and SBLI_SS store the 9 velocity
+ *    algorithm of §2.3.1).  Variants SBLI_RS and SBLI_SS store the 9 velocity
  *    gradients to arrays and evaluate the other derivatives on the fly,
  *    recomputed at each occurrence (RS) or once into thread-local variables
  *    (SS); SBLI_RA, SBLI_SN and SBLI_SN2 store nothing and recompute every
  *    derivative at each occurrence (RA), or evaluate each once into
  *    thread-local variables in listed order (SN) or grouped by velocity
  *    component (SN2): the paper's intermediate- and minimal-storage classes
- *    (§2.3), one thread per point, binary64 only, for comparison.
+ *    (§2.4, §2.5), one thread per point, binary64 only, for comparison.
  */
 #ifndef SBLI_H
 #define SBLI_H

@@ -1,6 +1,7 @@
 // algorithms.cu -- the paper's other evaluation strategies for the residual
-// of Eqs. 1-3 (§2.3.2-2.3.3), in binary64, as comparison variants beside the
-// store-all (BL) variant and the tiled fused kernel:
+// of Eqs. 1-3 (§2.4 intermediate storage, §2.5 minimal storage), in binary64,
+// as comparison variants beside the store-all (BL) variant and the tiled
+// fused kernel:
 //
 //   RS  Recompute Some: the 9 velocity gradients D_j u_i are stored to global
 //       arrays first (velocity arrays, then one derivative launch each, as BL

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libsbli.so")
 SBLI_OK, SBLI_EINVAL, SBLI_ENOMEM, SBLI_ECUDA, SBLI_ETIMEOUT, SBLI_EUNSUPPORTED = range(6)
 SBLI_FP64, SBLI_FP32, SBLI_FP32_DF, SBLI_DF64 = 0, 1, 2, 3
 SBLI_FUSED, SBLI_STORE_ALL, SBLI_RS, SBLI_SS, SBLI_RA, SBLI_SN, SBLI_SN2 = range(7)
-# the paper's algorithm names (§2.3) of each variant; "fused" is the tiled product kernel
+# the paper's algorithm names (§2.3-2.5) of each variant; "fused" is the tiled product kernel
 VARIANT_NAMES = {SBLI_FUSED: "fused", SBLI_STORE_ALL: "BL", SBLI_RS: "RS", SBLI_SS: "SS", SBLI_RA: "RA",
                  SBLI_SN: "SN", SBLI_SN2: "SN2"}
 
