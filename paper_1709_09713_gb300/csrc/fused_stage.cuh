@@ -142,8 +142,9 @@ __device__ __forceinline__ void store_rec(dfloat* p, const dfloat (&r)[NV]) {
 // 8-9 in columns 40+2s, 41+2s, so every access is aligned to its own width.
 // 32x32b shapes: each thread of the warp reads or writes its own lane.
 constexpr int TM_COLS_PER_WARP = 64;
-constexpr int TM_TAIL = 8 * NSLOT;
-static_assert(NV == 10 && TM_TAIL + 2 * NSLOT <= TM_COLS_PER_WARP, "z queue must fit the warp's TMEM window");
+constexpr int TM_TAIL = 8 * NSLOT;           // fields 8-9 of slot s: columns TM_TAIL + 2s, +1
+constexpr int TM_DIAG = TM_TAIL + 2 * NSLOT;  // D1_x u0, D1_y u1 of slot s: columns TM_DIAG + 2s, +1
+static_assert(NV == 10 && TM_DIAG + 2 * NSLOT <= TM_COLS_PER_WARP, "z queue must fit the warp's TMEM window");
 
 template <int NW>
 constexpr int tmem_columns() {
@@ -177,6 +178,29 @@ __device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, float (&r)
 #pragma unroll
   for (int i = 0; i < NV; ++i) r[i] = __uint_as_float(v[i]);
 }
+// the pair (D1_x u0, D1_y u1) of this thread's column in slot `slot`
+__device__ __forceinline__ void tmem_store_diag(uint32_t win, int slot, float d00, float d11) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(win + (uint32_t)(TM_DIAG + 2 * slot)),
+      "r"(__float_as_uint(d00)), "r"(__float_as_uint(d11))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_load_diag(uint32_t win, int slot, float& d00, float& d11) {
+  uint32_t a, b;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(a), "=r"(b)
+      : "r"(win + (uint32_t)(TM_DIAG + 2 * slot))
+      : "memory");
+  d00 = __uint_as_float(a);
+  d11 = __uint_as_float(b);
+}
+template <typename T>
+__device__ __forceinline__ void tmem_store_diag(uint32_t, int, T, T) {}
+template <typename T>
+__device__ __forceinline__ void tmem_load_diag(uint32_t, int, T&, T&) {}
 __device__ __forceinline__ void tmem_load_rec(uint32_t, int, double (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const double (&)[NV]) {}
 __device__ __forceinline__ void tmem_load_rec(uint32_t, int, dfloat (&)[NV]) {}
@@ -425,6 +449,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   const int nit = nplanes + 4;
   const uint32_t twin = ZT ? tmem_window(tmem_base) : 0u;
   T d22 = T(0);
+  T g00c = T(0), g11c = T(0);  // D1_x u0, D1_y u1 at the centre point
 
   // halo tasks of phase 2b, fixed for the whole z march: s_0 on the x0-halo
   // columns (4*TY points) and s_1 on the x1-halo rows (4*TX points)
@@ -529,8 +554,12 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
                         -c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]));
       const T d11 = mad(c.c1[1], R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1],
                         -c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]));
-      sm.dring[se][0][ty][tx] = d00;
-      sm.dring[se][1][ty][tx] = d11;
+      if constexpr (ZT) {
+        tmem_store_diag(twin, se, d00, d11);  // this thread's column only
+      } else {
+        sm.dring[se][0][ty][tx] = d00;
+        sm.dring[se][1][ty][tx] = d11;
+      }
     }
     if (it < 4) continue;  // ring not yet full; slots written so far are not read again before the next sync
 
@@ -571,8 +600,14 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
                    -c.c2[2] * (sm.ring[sl[4]][yy][xx][V_U2] - sm.ring[sl[0]][yy][xx][V_U2]));
       };
       d22 = u2z(sy, sx);
-      sm.s0buf[ty][sx] = sm.dring[scen][1][ty][tx] + d22;
-      sm.s1buf[sy][tx] = sm.dring[scen][0][ty][tx] + d22;
+      if constexpr (ZT) {
+        tmem_load_diag(twin, scen, g00c, g11c);
+      } else {
+        g00c = sm.dring[scen][0][ty][tx];
+        g11c = sm.dring[scen][1][ty][tx];
+      }
+      sm.s0buf[ty][sx] = g11c + d22;
+      sm.s1buf[sy][tx] = g00c + d22;
       const T(*R)[SX][NV] = sm.ring[scen];
 #pragma unroll
       for (int j = 0; j < HPT; ++j) {
@@ -609,8 +644,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         t.rM[i] = T(0);
         t.lap[i] = T(0);
       }
-      t.g[0][0] = sm.dring[scen][0][ty][tx];
-      t.g[1][1] = sm.dring[scen][1][ty][tx];
+      t.g[0][0] = g00c;
+      t.g[1][1] = g11c;
       t.g[2][2] = d22;
 
       // x0 group first (SN2 ordering), then x1, x2
@@ -632,7 +667,15 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           if (ZT) tmem_load_rec(twin, zs[k], r);
           else load_rec(&sm.ring[zs[k]][sy][sx][0], r);
         };
-        auto sf = [&](int k, const T(&)[NV]) { return sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx]; };
+        auto sf = [&](int k, const T(&)[NV]) {
+          if constexpr (ZT) {
+            T a, b;
+            tmem_load_diag(twin, zs[k], a, b);
+            return a + b;
+          } else {
+            return sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx];
+          }
+        };
         axis_terms<2>(ld, sf, c, uc, t);
       }
 
