@@ -68,7 +68,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32df", "df64"],
+                    help="main line precision: binary64 (default), binary32 storage with a binary64 or "
+                         "double-float accumulator, or binary64 storage with double-float arithmetic")
     ap.add_argument("--variant", default="fused", choices=["fused", "store_all"])
     ap.add_argument("--alg-steps", type=int, default=24,
                     help="steps per algorithm class in the comparison leg (>= ~1 s each for NVML energy)")
@@ -459,7 +461,7 @@ def run_ours(args):
     if not os.path.exists(S.LIB_PATH):
         B.build()
     S.lib()
-    prec = S.SBLI_FP64 if args.precision == "fp64" else S.SBLI_FP32
+    prec = PRECISIONS[args.precision]
     var = S.SBLI_FUSED if args.variant == "fused" else S.SBLI_STORE_ALL
     n, dt, P = args.n, args.dt, args.n**3
     stream = torch.cuda.Stream()
@@ -513,8 +515,18 @@ def run_ours(args):
                 "note": f"binary64 pipe; {FUSED_FP64_FLOP_PER_PT:.0f} flop/pt-stage counted by ncu; peak = {sms} SMs x "
                         f"4 flop/clk x {clock_ghz:.3f} GHz (median SM clock under load)",
                 "hbm_frac": ALG_BYTES["fp64"] * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    elif prec == S.SBLI_DF64 and var == S.SBLI_FUSED and DF64_INST_PER_PT:
+        clock_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = sms * 4 * 32 * clock_ghz * 1e9
+        ach = DF64_INST_PER_PT * P / (stage_ms / 1e3)
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "thread-instr/s", "frac": ach / peak,
+                "traffic": None,
+                "note": f"binary32 issue: {DF64_INST_PER_PT:.0f} instructions per pt-stage (ncu); peak = {sms} SMs x "
+                        f"4 sub-partitions x 32 lanes x {clock_ghz:.3f} GHz",
+                "hbm_frac": ALG_BYTES["df64"] * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
     else:
-        pname = "fp64" if prec == S.SBLI_FP64 else "fp32"
+        pname = args.precision
         ach = ALG_BYTES[pname] * P / (stage_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC.get((pname, n)) if var == S.SBLI_FUSED else None,
@@ -531,7 +543,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == S.SBLI_FP64 else "f32 (f64 accumulator)",
+        "dtype": {"fp64": "f64", "fp32": "f32 (f64 accumulator)", "fp32df": "f32 (f32-pair accumulator)",
+                  "df64": "f32 pairs (double-float), f64 storage"}[args.precision],
         "data": "synthetic (Taylor-Green vortex initial field of section 4)",
         "config": {"workload": f"TGV {n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, Pr 0.71, dt {dt}",
                    "grid": [n, n, n], "l2": f"inputs larger than L2 ({state_bytes / 2**20:.0f} MiB state register)",
