@@ -120,16 +120,17 @@ struct sbli_grid {
 namespace {
 
 // CTAs per SM a tile height allows (shared memory bound).
-int ctas_per_sm(int precision, int ty, int px = 1) {
-  return (f64_registers(precision) || ty >= 16 || px == 2) ? 1 : 2;
+int ctas_per_sm(int precision, int ty, int px = 1, int zq = 0) {
+  if (f64_registers(precision) || ty >= 16 || px == 2) return 1;
+  return zq ? 3 : 2;  // the TMEM z queue keeps 3 full-record planes in shared memory
 }
 
 // Planes per CTA ranked by a wave-balance model: cost = waves * (zc + 1.5),
 // the 4 warm-up planes of a z segment costing about 1.5 full planes.
-void rank_zc(const Geom& g, int precision, int ty, int* best, int nbest, int px = 1) {
+void rank_zc(const Geom& g, int precision, int ty, int* best, int nbest, int px = 1, int zq = 0) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long slots = (long long)sms * ctas_per_sm(precision, ty, px);
+  const long long slots = (long long)sms * ctas_per_sm(precision, ty, px, zq);
   const int w = 32 * px;
   const long long tiles = (long long)((g.n0 + w - 1) / w) * ((g.n1 + ty - 1) / ty);
   double cost[8];
@@ -674,7 +675,7 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int*
       for (int t = 0; t < 2; ++t) {
         if (!valid_config(g->precision, tys[t], 4, zq, px)) continue;
         int zc[3];
-        rank_zc(g->geom, g->precision, tys[t], zc, 3, px);
+        rank_zc(g->geom, g->precision, tys[t], zc, 3, px, zq);
         for (int i = 0; i < 3; ++i) {
           bool dup = false;
           const int z = std::max(4, std::min(zc[i], g->geom.n2));

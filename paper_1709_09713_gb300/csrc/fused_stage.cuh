@@ -51,11 +51,18 @@ constexpr int NSLOT = 5;
 // primitive values of one point record in a ring slot
 enum { V_RHO, V_M0, V_M1, V_M2, V_E, V_U0, V_U1, V_U2, V_P, V_T, NV };
 
-template <typename T, int TY>
+// ZT (binary32 with the TMEM z queue): the x2 neighbours of a thread's own
+// column come from tensor memory, so shared memory keeps full records only
+// for the planes that are still to become the centre (entering, middle,
+// centre: 3 slots), u_2 alone on the five ring planes (for D1_z u_2 on the
+// halo), and no D1_x u0 / D1_y u1 ring.
+template <typename T, int TY, bool ZT = false>
 struct FusedSmem {
   static constexpr int SY = TY + 2 * HALO;
-  T ring[NSLOT][SY][SX][NV];  // rho', m_i, E', u_i, p', T' per haloed point
-  T dring[NSLOT][2][TY][TX];  // D1_x u0 and D1_y u1 per plane (tile only)
+  static constexpr int NFULL = ZT ? 3 : NSLOT;
+  T ring[NFULL][SY][SX][NV];        // rho', m_i, E', u_i, p', T' per haloed point
+  T u2ring[ZT ? NSLOT : 1][SY][SX];  // u_2 per haloed point (ZT)
+  T dring[ZT ? 1 : NSLOT][2][TY][TX];  // D1_x u0 and D1_y u1 per plane (tile only; not ZT)
   T s0buf[TY][SX];            // s_0 = D1_y u1 + D1_z u2, centre plane, x0-haloed rows
   T s1buf[SY][TX];            // s_1 = D1_x u0 + D1_z u2, centre plane, x1-haloed columns
   double red[2][32];          // block reduction of (ke, enstrophy)
@@ -352,13 +359,64 @@ __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, cons
 #undef SBLI_D1
 }
 
+// The same terms with the four neighbours streamed through registers one at
+// a time: each neighbour's record is folded into the accumulators with its
+// stencil weights (Eq. 6: +c2, -c1, +c1, -c2; Eq. 7 off-centre: e2, e1, e1,
+// e2 for offsets -2, -1, +1, +2), so only one record is live.  Fewer
+// operations than the difference-first form for hardware FMA types; the
+// double-float type keeps the difference-first form (its products cost more
+// than its sums).
+template <int A, typename T, typename LD, typename SF>
+__device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfun, const Coef<T>& c,
+                                                  const T (&uc)[3], Terms<T>& t) {
+  const T c1 = c.c1[A], c2 = c.c2[A], e1 = c.e1[A], e2 = c.e2[A];
+  const T ua = uc[A];
+  T gA = T(0);                        // sum_k (e_k u_A,k + c_k s_k): G_A without its centre term
+  T gI[3] = {T(0), T(0), T(0)};      // D1_A u_i, i != A
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T cd = (k == 0) ? c2 : (k == 1) ? -c1 : (k == 2) ? c1 : -c2;
+    const T ed = (k == 0 || k == 3) ? e2 : e1;
+    T r[NV];
+    ldrec(k, r);
+    const T sk = sfun(k, r);
+    const T w = cd * (r[V_U0 + A] + ua);        // D1(f (u_A + u_A^c)) weight
+    const T x2 = (cd + cd) * r[V_U0 + A];       // 2 x D1(f u_A) weight
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t.rM[i] = mad(w, r[V_M0 + i], t.rM[i]);
+    t.rM[A] = mad(cd + cd, r[V_P], t.rM[A]);
+    t.rE = mad(w, r[V_E], mad(x2, r[V_P], t.rE));
+    t.rrho = mad(cd, fma(ua, r[V_RHO], r[V_M0 + A]), t.rrho);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t.lap[i] = mad(ed, r[V_U0 + i], t.lap[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i != A) gI[i] = mad(cd, r[V_U0 + i], gI[i]);
+    gA = mad(ed, r[V_U0 + A], mad(cd, sk, gA));
+    t.lapT = mad(ed, r[V_T], t.lapT);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (i != A) t.g[i][A] = gI[i];
+  t.G[A] = fma(c.e0[A], uc[A], gA);
+}
+
+template <int A, typename T, typename LD, typename SF>
+__device__ __forceinline__ void axis_terms_any(const LD& ldrec, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
+                                               Terms<T>& t) {
+  if constexpr (std::is_same<T, dfloat>::value)
+    axis_terms<A>(ldrec, sfun, c, uc, t);
+  else
+    axis_terms_stream<A>(ldrec, sfun, c, uc, t);
+}
+
 // TIN: type of the stage input in HBM; TOUT: type of the stage output.
 // CTAs per SM the launch bounds plan for: shared memory allows two 32 x 8
 // binary32 CTAs per SM (97.5 KiB each); binary64 (194.5 KiB) and 32 x 16
 // tiles take one.
-template <typename T, int TY>
+template <typename T, int TY, bool ZT = false>
 constexpr int fused_min_blocks() {
-  return (sizeof(T) == 4 && TY <= 8) ? 2 : 1;
+  return (sizeof(T) == 4 && TY <= 8) ? (ZT ? 3 : 2) : 1;
 }
 // tile width in points: 32 columns per warp row, times the columns per thread
 template <typename T>
@@ -374,9 +432,9 @@ constexpr int tile_width() {
 template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
           bool ZT = false>
 __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c, int bx, int by, int zbeg, int zend_req,
-                                            FusedSmem<T, TY>& sm, double& ke_acc, double& ens_acc,
+                                            FusedSmem<T, TY, ZT>& sm, double& ke_acc, double& ens_acc,
                                             uint32_t tmem_base = 0) {
-  using S = FusedSmem<T, TY>;
+  using S = FusedSmem<T, TY, ZT>;
   constexpr int SY = S::SY;
   constexpr int NT = TX * TY;
   constexpr int PTS = SX * SY;
@@ -482,6 +540,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   int rs[NSLOT];
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) rs[k] = (k + 1) % NSLOT;  // any permutation; warm-up fills all slots
+  // full-record slots of planes e-2, e-1, e (ZT; otherwise the ring slots)
+  int rf[3] = {1, 2, 0};
 
   TIN pf[LPT][NF][PP];
   auto issue_loads = [&](int it_load) {
@@ -511,8 +571,15 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       rs[NSLOT - 1] = t0;
     }
     const int se = rs[NSLOT - 1];
+    if constexpr (ZT) {
+      const int t0 = rf[0];
+      rf[0] = rf[1];
+      rf[1] = rf[2];
+      rf[2] = t0;
+    }
+    const int fe = ZT ? rf[2] : se;  // full-record slot of the entering plane
     {
-      T* ring = &sm.ring[se][0][0][0];
+      T* ring = &sm.ring[fe][0][0][0];
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
         if (l == 0 || ld_off[l][0] >= 0) {  // the own point is always loaded
@@ -538,7 +605,10 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           rec[V_P] = p_p;
           rec[V_T] = T_p;
           store_rec(ring + ld_s[l] * NV, rec);
-          if (ZT && l == 0) tmem_store_rec(twin, se, rec);  // l == 0: every thread
+          if constexpr (ZT) {
+            (&sm.u2ring[se][0][0])[ld_s[l]] = u2;
+            if (l == 0) tmem_store_rec(twin, se, rec);  // l == 0: every thread
+          }
         }
       }
     }
@@ -548,7 +618,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     // in-plane diagonal gradients of the entering plane, kept for s_2 and
     // for the velocity gradient when the plane is the centre.
     {
-      const T(*R)[SX][NV] = sm.ring[se];
+      const T(*R)[SX][NV] = sm.ring[fe];
       const int sy = ty + HALO, sx = tx + HALO;
       const T d00 = mad(c.c1[0], R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0],
                         -c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]));
@@ -567,6 +637,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     // slot of plane zc + o, o = -2..2
     const int sl[5] = {rs[0], rs[1], rs[2], rs[3], rs[4]};
     const int scen = sl[2];
+    const int fc = ZT ? rf[0] : scen;  // full-record slot of the centre plane
     unsigned oc[PP];  // offsets of the thread's centre points
 #pragma unroll
     for (int j = 0; j < PP; ++j) oc[j] = (unsigned)zc * plane + own[j];
@@ -595,9 +666,15 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     // s_0 and s_1 on the centre plane's tile and halo.
     {
       const int sy = ty + HALO, sx = tx + HALO;
+      auto u2at = [&](int slot, int yy, int xx) {
+        if constexpr (ZT)
+          return sm.u2ring[slot][yy][xx];
+        else
+          return sm.ring[slot][yy][xx][V_U2];
+      };
       auto u2z = [&](int yy, int xx) {
-        return mad(c.c1[2], sm.ring[sl[3]][yy][xx][V_U2] - sm.ring[sl[1]][yy][xx][V_U2],
-                   -c.c2[2] * (sm.ring[sl[4]][yy][xx][V_U2] - sm.ring[sl[0]][yy][xx][V_U2]));
+        return mad(c.c1[2], u2at(sl[3], yy, xx) - u2at(sl[1], yy, xx),
+                   -c.c2[2] * (u2at(sl[4], yy, xx) - u2at(sl[0], yy, xx)));
       };
       d22 = u2z(sy, sx);
       if constexpr (ZT) {
@@ -608,7 +685,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       }
       sm.s0buf[ty][sx] = g11c + d22;
       sm.s1buf[sy][tx] = g00c + d22;
-      const T(*R)[SX][NV] = sm.ring[scen];
+      const T(*R)[SX][NV] = sm.ring[fc];
 #pragma unroll
       for (int j = 0; j < HPT; ++j) {
         const int hy = hxy[j] >> 8, hx = hxy[j] & 0xFF;
@@ -627,10 +704,12 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     // ---------------------------------------------------------------- phase 3
     {
       const int sy = ty + HALO, sx = tx + HALO;
-      const T(*C)[SX][NV] = sm.ring[scen];
+      const T(*C)[SX][NV] = sm.ring[fc];
       T cen[NV];
-      if (ZT) tmem_load_rec(twin, scen, cen);
-      else load_rec(&C[sy][sx][0], cen);
+      if constexpr (ZT)
+        tmem_load_rec(twin, scen, cen);
+      else
+        load_rec(&C[sy][sx][0], cen);
       const T rho_p = cen[V_RHO];
       const T mc[3] = {cen[V_M0], cen[V_M1], cen[V_M2]};
       const T Ec = cen[V_E];
@@ -653,19 +732,21 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         const int off[4] = {-2, -1, 1, 2};
         auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy][sx + off[k]][0], r); };
         auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[ty][sx + off[k]]; };
-        axis_terms<0>(ld, sf, c, uc, t);
+        axis_terms_any<0>(ld, sf, c, uc, t);
       }
       {
         const int off[4] = {-2, -1, 1, 2};
         auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy + off[k]][sx][0], r); };
         auto sf = [&](int k, const T(&)[NV]) { return sm.s1buf[sy + off[k]][tx]; };
-        axis_terms<1>(ld, sf, c, uc, t);
+        axis_terms_any<1>(ld, sf, c, uc, t);
       }
       {
         const int zs[4] = {sl[0], sl[1], sl[3], sl[4]};
         auto ld = [&](int k, T(&r)[NV]) {
-          if (ZT) tmem_load_rec(twin, zs[k], r);
-          else load_rec(&sm.ring[zs[k]][sy][sx][0], r);
+          if constexpr (ZT)
+            tmem_load_rec(twin, zs[k], r);
+          else
+            load_rec(&sm.ring[zs[k]][sy][sx][0], r);
         };
         auto sf = [&](int k, const T(&)[NV]) {
           if constexpr (ZT) {
@@ -676,7 +757,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             return sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx];
           }
         };
-        axis_terms<2>(ld, sf, c, uc, t);
+        axis_terms_any<2>(ld, sf, c, uc, t);
       }
 
       // assemble Eqs. 1-3
@@ -791,10 +872,10 @@ __device__ __forceinline__ void block_reduce_pair(double (&red)[2][32], double k
 // Single grid: one CTA per (tile, z chunk).  ZT: x2-neighbour records in TMEM.
 template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
           bool ZT = false>
-__global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
+__global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     fused_stage_kernel(const StageArgs a, const Coef<T> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FusedSmem<T, TY>& sm = *reinterpret_cast<FusedSmem<T, TY>*>(smem_raw);
+  FusedSmem<T, TY, ZT>& sm = *reinterpret_cast<FusedSmem<T, TY, ZT>*>(smem_raw);
   constexpr int NCOL = tmem_columns<TY>();  // TX*TY/32 = TY warps
   uint32_t tbase = 0;
   if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
@@ -818,7 +899,7 @@ template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool W
           bool ZT = false>
 cudaError_t launch_fused_t(const StageArgs& a, const Coef<T>& c, cudaStream_t s) {
   auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF, ZT>;
-  const size_t smem = sizeof(FusedSmem<T, TY>);
+  const size_t smem = sizeof(FusedSmem<T, TY, ZT>);
   static bool configured = false;  // one attribute call per instantiation
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
