@@ -21,11 +21,16 @@
 
 namespace sbli {
 
-template <typename T, typename TIN, typename TOUT, int TY, bool WITH_KE>
-__global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
+// ZT: x2-neighbour records in a TMEM queue and the 3-slot shared ring (binary32),
+// the CTA's TMEM columns held for all of its work items.
+template <typename T, typename TIN, typename TOUT, int TY, bool WITH_KE, bool ZT = false>
+__global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     batch_stage_kernel(const __grid_constant__ BatchParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FusedSmem<T, TY>& sm = *reinterpret_cast<FusedSmem<T, TY>*>(smem_raw);
+  FusedSmem<T, TY, ZT>& sm = *reinterpret_cast<FusedSmem<T, TY, ZT>*>(smem_raw);
+  constexpr int NCOL = tmem_columns<TY>();
+  uint32_t tbase = 0;
+  if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
   for (long long item = blockIdx.x; item < p.total_items; item += gridDim.x) {
     // member owning this item (binary search over item_begin)
     int lo = 0, hi = p.count - 1;
@@ -42,9 +47,11 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY>())
     const int bx = tile % p.tiles_x[lo], by = tile / p.tiles_x[lo];
     const int zbeg = chunk * a.zc;
     double ke = 0.0, ens = 0.0;
-    fused_march<T, TIN, TOUT, TY, false, WITH_KE>(a, p.c[lo], bx, by, zbeg, zbeg + a.zc, sm, ke, ens);
+    fused_march<T, TIN, TOUT, TY, false, WITH_KE, false, ZT>(a, p.c[lo], bx, by, zbeg, zbeg + a.zc, sm, ke, ens,
+                                                               tbase);
     if (WITH_KE) block_reduce_pair<TX * TY>(sm.red, ke, ens, p.ke_items + 2 * item);
   }
+  if (ZT) tmem_release<NCOL>(tbase);
 }
 
 // Per member: fixed-order sum of its items' partials, scaled by 1/P.
@@ -66,25 +73,27 @@ __global__ void __launch_bounds__(256) batch_ke_finalize(const double* __restric
 }
 
 // ---- launchers (declared in batch_kernel.cuh)
+// binary32 members: TMEM z queue and 3-slot ring, 3 CTAs per SM (the grid is
+// sized for that by the caller: batch_ctas_per_sm)
 template <>
 cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(FusedSmem<float, 8>);
+  const size_t smem = sizeof(FusedSmem<float, 8, true>);
   static bool cfg = false;
   if (!cfg) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, false>,
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, false, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, true>,
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, true, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, float, float, 8, false>,
+    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, float, float, 8, false, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     cfg = true;
   }
   if (in64) {
-    if (p.ke_items) batch_stage_kernel<float, double, float, 8, true><<<grid, TX * 8, smem, s>>>(p);
-    else batch_stage_kernel<float, double, float, 8, false><<<grid, TX * 8, smem, s>>>(p);
+    if (p.ke_items) batch_stage_kernel<float, double, float, 8, true, true><<<grid, TX * 8, smem, s>>>(p);
+    else batch_stage_kernel<float, double, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
   } else {
-    batch_stage_kernel<float, float, float, 8, false><<<grid, TX * 8, smem, s>>>(p);
+    batch_stage_kernel<float, float, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
   }
   return cudaGetLastError();
 }
@@ -395,7 +404,7 @@ int sbli_batch_create(sbli_batch** out, int count, const int* n, const sbli_para
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->grid_ctas = sms * (batch_f64_registers(precision) ? 1 : 2);
+  b->grid_ctas = sms * batch_ctas_per_sm(precision);
   // per-member constants for the KE finalisation
   std::vector<double> inv(count);
   std::vector<long long> beg(count + 1);

@@ -25,6 +25,11 @@ struct BatchParams {
 template <typename T>
 cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStream_t s);
 
+// Resident CTAs per SM of the multi-member launch: binary32 members run the
+// TMEM-queue kernel (64 KiB shared, 80 registers: 3 per SM), binary64 and
+// double-float members the 194.5 KiB shared-ring kernel (1 per SM).
+inline int batch_ctas_per_sm(int precision) { return precision == SBLI_FP32 ? 3 : 1; }
+
 // Work items (z chunk x 32 x 8 tile) of one member and its planes per item.
 inline int batch_zc(int n2) { return n2 < 32 ? n2 : 32; }
 inline long long member_items(const int n[3]) {

@@ -278,8 +278,8 @@ int sbli_server_create(sbli_server** out, void* arena, size_t arena_bytes, int m
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  s->grid64 = sms;
-  s->grid32 = 2 * sms;
+  s->grid64 = sms * batch_ctas_per_sm(SBLI_FP64);
+  s->grid32 = sms * batch_ctas_per_sm(SBLI_FP32);
   s->t0 = std::chrono::steady_clock::now();
   *out = s;
   return SBLI_OK;
