@@ -373,6 +373,12 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
   const T ua = uc[A];
   T gA = T(0);                        // sum_k (e_k u_A,k + c_k s_k): G_A without its centre term
   T gI[3] = {T(0), T(0), T(0)};      // D1_A u_i, i != A
+  // binary64 (bound by its FMA pipe): the per-axis products c u_A^c and the
+  // doubled weights 2c once, so each neighbour's weights are one FMA / one
+  // multiply; binary32 keeps the register-leaner per-neighbour form
+  constexpr bool PRE = std::is_same<T, double>::value;
+  const T cu1 = PRE ? c1 * ua : T(0), cu2 = PRE ? c2 * ua : T(0);
+  const T c1x2 = PRE ? c1 + c1 : T(0), c2x2 = PRE ? c2 + c2 : T(0);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const T cd = (k == 0) ? c2 : (k == 1) ? -c1 : (k == 2) ? c1 : -c2;
@@ -380,11 +386,19 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
     T r[NV];
     ldrec(k, r);
     const T sk = sfun(k, r);
-    const T w = cd * (r[V_U0 + A] + ua);        // D1(f (u_A + u_A^c)) weight
-    const T x2 = (cd + cd) * r[V_U0 + A];       // 2 x D1(f u_A) weight
+    T w, cd2;
+    if constexpr (PRE) {
+      const T cdu = (k == 0) ? cu2 : (k == 1) ? -cu1 : (k == 2) ? cu1 : -cu2;
+      w = fma(cd, r[V_U0 + A], cdu);            // D1(f (u_A + u_A^c)) weight
+      cd2 = (k == 0) ? c2x2 : (k == 1) ? -c1x2 : (k == 2) ? c1x2 : -c2x2;
+    } else {
+      w = cd * (r[V_U0 + A] + ua);
+      cd2 = cd + cd;
+    }
+    const T x2 = cd2 * r[V_U0 + A];             // 2 x D1(f u_A) weight
 #pragma unroll
     for (int i = 0; i < 3; ++i) t.rM[i] = mad(w, r[V_M0 + i], t.rM[i]);
-    t.rM[A] = mad(cd + cd, r[V_P], t.rM[A]);
+    t.rM[A] = mad(cd2, r[V_P], t.rM[A]);
     t.rE = mad(w, r[V_E], mad(x2, r[V_P], t.rE));
     t.rrho = mad(cd, fma(ua, r[V_RHO], r[V_M0 + A]), t.rrho);
 #pragma unroll
