@@ -60,9 +60,11 @@ template <typename T, int TY, bool ZT = false>
 struct FusedSmem {
   static constexpr int SY = TY + 2 * HALO;
   static constexpr int NFULL = ZT ? 3 : NSLOT;
-  T ring[NFULL][SY][SX][NV];        // rho', m_i, E', u_i, p', T' per haloed point
-  T u2ring[ZT ? NSLOT : 1][SY][SX];  // u_2 per haloed point (ZT)
-  T dring[ZT ? 1 : NSLOT][2][TY][TX];  // D1_x u0 and D1_y u1 per plane (tile only; not ZT)
+  T ring[NFULL][SY][SX][NV];  // rho', m_i, E', u_i, p', T' per haloed point
+  union {
+    T u2ring[NSLOT][SY][SX];    // ZT: u_2 per haloed point of the five ring planes
+    T dring[NSLOT][2][TY][TX];  // otherwise: D1_x u0 and D1_y u1 per plane (tile only)
+  };
   T s0buf[TY][SX];            // s_0 = D1_y u1 + D1_z u2, centre plane, x0-haloed rows
   T s1buf[SY][TX];            // s_1 = D1_x u0 + D1_z u2, centre plane, x1-haloed columns
   double red[2][32];          // block reduction of (ke, enstrophy)
