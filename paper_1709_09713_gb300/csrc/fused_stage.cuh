@@ -521,7 +521,9 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
 
   const int nplanes = zend - zbeg;
   const int nit = nplanes + 4;
-  const uint32_t twin = ZT ? tmem_window(tmem_base) : 0u;
+  // the window address is warp-uniform; broadcasting lane 0's copy lets the
+  // compiler keep it in a uniform register for the tcgen05 operands
+  const uint32_t twin = ZT ? __shfl_sync(0xffffffffu, tmem_window(tmem_base), 0) : 0u;
   T d22 = T(0);
   T g00c = T(0), g11c = T(0);  // D1_x u0, D1_y u1 at the centre point
 
