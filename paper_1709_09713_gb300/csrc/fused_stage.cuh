@@ -566,7 +566,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     const unsigned zoff = (unsigned)wrapi(zbeg - HALO + it_load, n2) * plane;
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
-      if (ld_off[l][0] >= 0) {
+      if (l == 0 || ld_off[l][0] >= 0) {  // the own point always exists
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
           const unsigned o = zoff + (unsigned)ld_off[l][j];
@@ -803,6 +803,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       for (int j = 0; j < PP; ++j) {
         if (!valid[j]) continue;
         const unsigned o = oc[j];
+        TOUT qo[NF];
         if constexpr (RHS_ONLY) {
 #pragma unroll
           for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o] = double(lane(R[f], j));
@@ -824,7 +825,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             const float lo3 = __fsub_rn(lo2, __fsub_rn(hi3, s));
             a.dacc_out[(long long)f * a.g.P + o] = hi3;
             a.dacc_out[(long long)(NF + f) * a.g.P + o] = lo3;
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = TOUT(hi3 + fmaf(ambdt, r, lo3));
+            qo[f] = TOUT(hi3 + fmaf(ambdt, r, lo3));
           }
         } else if constexpr (is_f64_class<T>()) {
           // binary64 (or double-float) stage: acc + b dt R and acc + a dt R,
@@ -833,7 +834,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           for (int f = 0; f < NF; ++f) {
             const double r = as_double(R[f]);
             a.acc_out[(long long)f * a.g.P + o] = fma(a.b_dt, r, accv[f][j]);
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = TOUT(fma(a.a_dt, r, accv[f][j]));
+            qo[f] = TOUT(fma(a.a_dt, r, accv[f][j]));
           }
         } else {
           // binary32 stage, binary64 accumulator: one DADD per field,
@@ -845,7 +846,13 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             const float r = float(lane(R[f], j));
             const double accn = accv[f][j] + widen_f32_fast(bdt * r);
             a.acc_out[(long long)f * a.g.P + o] = accn;
-            if (a.q_out) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = TOUT(narrow_f64_fast(accn) + ambdt * r);
+            qo[f] = TOUT(narrow_f64_fast(accn) + ambdt * r);
+          }
+        }
+        if constexpr (!RHS_ONLY) {
+          if (a.q_out) {  // the stage field (absent on the last stage)
+#pragma unroll
+            for (int f = 0; f < NF; ++f) static_cast<TOUT*>(a.q_out)[(long long)f * a.g.P + o] = qo[f];
           }
         }
         if (WITH_KE) {
