@@ -660,25 +660,28 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
 #pragma unroll
     for (int j = 0; j < PP; ++j) oc[j] = (unsigned)zc * plane + own[j];
 
-    // accumulator of the centre points, fetched before the arithmetic
+    // accumulator of the centre points (fetched during phase 3, after the
+    // x0 terms, so that its latency overlaps the x1 and x2 terms)
     double accv[NF][PP];
     float dhi[NF][PP], dlo[NF][PP];  // double-float accumulator (DF mode)
-    if (!RHS_ONLY) {
+    auto fetch_acc = [&]() {
+      if (!RHS_ONLY) {
 #pragma unroll
-      for (int j = 0; j < PP; ++j) {
-        if (!valid[j]) continue;
-        if (DF) {
+        for (int j = 0; j < PP; ++j) {
+          if (!valid[j]) continue;
+          if (DF) {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            dhi[f][j] = a.dacc_in[(long long)f * a.g.P + oc[j]];
-            dlo[f][j] = a.dacc_in[(long long)(NF + f) * a.g.P + oc[j]];
+            for (int f = 0; f < NF; ++f) {
+              dhi[f][j] = a.dacc_in[(long long)f * a.g.P + oc[j]];
+              dlo[f][j] = a.dacc_in[(long long)(NF + f) * a.g.P + oc[j]];
+            }
+          } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) accv[f][j] = accf[f] ? accf[f][oc[j]] : double(qf[f][oc[j]]);
           }
-        } else {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) accv[f][j] = accf[f] ? accf[f][oc[j]] : double(qf[f][oc[j]]);
         }
       }
-    }
+    };
 
     // --------------------------------------------------------------- phase 2b
     // s_0 and s_1 on the centre plane's tile and halo.
@@ -752,6 +755,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[ty][sx + off[k]]; };
         axis_terms_any<0>(ld, sf, c, uc, t);
       }
+      fetch_acc();
       {
         const int off[4] = {-2, -1, 1, 2};
         auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy + off[k]][sx][0], r); };
