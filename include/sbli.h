@@ -194,12 +194,15 @@ SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, in
  * binary32 grids 8 or 16), planes per CTA along x2 (>= 4) and, for the
  * binary32 paths, where each thread keeps its column's records of the five
  * x2 planes (z_queue = 0: the shared-memory ring; 1: a per-thread queue in
- * Blackwell tensor memory) and how many columns each thread owns
- * (columns_per_thread = 1, or 2: columns x and x + 32 of a 64 x 8 tile
- * computed together; shared-memory ring only).  Every configuration gives
- * bitwise the same state.  set_config validates and applies it (cached step
- * graphs are rebuilt); must be called at a step boundary.  z_queue and
- * columns_per_thread may be NULL in get_config. */
+ * Blackwell tensor memory, with only three full-record planes in shared
+ * memory) and how many columns each thread owns (columns_per_thread = 1, or
+ * 2: columns x and x + 32 of a 64 x 8 tile computed together in packed
+ * two-lane FP32 instructions; shared-memory ring only).  Tile height, planes
+ * per CTA and z_queue give bitwise the same state; two columns per thread
+ * fuse multiply-adds differently (bitwise equal among themselves, within the
+ * binary32 tolerance of one column).  set_config validates and applies it
+ * (cached step graphs are rebuilt); must be called at a step boundary.
+ * z_queue and columns_per_thread may be NULL in get_config. */
 SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue,
                              int* columns_per_thread);
 SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue, int columns_per_thread);

@@ -17,9 +17,19 @@
 //     conserved variables loaded from HBM (periodic wrap in the index
 //     arithmetic replaces the boundary pass of Fig. 1);
 //   * the loads of the next entering plane are issued as soon as the current
-//     plane is stored, and the centre plane's accumulator values before the
-//     residual is assembled, so HBM latency overlaps the arithmetic;
+//     plane is stored, and the centre plane's accumulator values after the
+//     x0 terms, so HBM latency overlaps the arithmetic;
 //   * x0/x1 derivatives read the centre slot, x2 derivatives read the ring;
+//     each axis streams its four neighbour records through the accumulators
+//     one at a time (axis_terms_stream; the double-float type keeps the
+//     difference-first form, axis_terms);
+//   * ZT (binary32): each thread keeps its own column's records of the five
+//     ring planes, and their D1_x u0 / D1_y u1, in tensor memory (TMEM), so
+//     the x2 derivatives read TMEM and shared memory keeps full records only
+//     for the entering, middle and centre planes, plus u_2 of the five planes
+//     for D1_z u_2 on the halo: 64 KiB per 32 x 8 CTA, three CTAs per SM;
+//   * the arithmetic type T is double, float, dfloat (double-float, binary64
+//     storage) or f32x2 (two columns per thread in packed FP32x2 instructions);
 //   * the mixed second derivatives of the stress divergence use, for each i,
 //       sum_{j != i} d2 u_j/dx_i dx_j = D1_i( s_i ),  s_i = sum_{j != i} D1_j u_j,
 //     (linearity of D1_i; the D1_a o D1_b reading of the mixed term), so
