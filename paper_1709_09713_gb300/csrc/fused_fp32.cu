@@ -1,7 +1,9 @@
 // fused_fp32.cu -- binary32 instantiations of the fused stage kernel.  The
 // stage input is binary64 at stage 0 (the state between steps) and binary32
-// at stages 1-2; the accumulator is always binary64.  Tiles 32 x 8 (two CTAs
-// per SM) and 32 x 16 (one CTA of 16 warps per SM).
+// at stages 1-2; the accumulator is binary64 or, for the double-float mode,
+// a hi/lo binary32 pair.  Tiles 32 x 8 (two CTAs per SM) and 32 x 16 (one
+// CTA of 16 warps per SM); the TMEM-queue and two-column kernels are in
+// their own files.
 #include "fused_stage.cuh"
 
 namespace sbli {

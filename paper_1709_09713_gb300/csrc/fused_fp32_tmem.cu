@@ -1,6 +1,7 @@
 // fused_fp32_tmem.cu -- binary32 stage kernels whose x2-neighbour records
 // come from a per-thread queue in tensor memory instead of the shared-memory
-// ring (both accumulator kinds, tiles 32 x 8 and 32 x 16).
+// ring, with three full-record planes in shared memory (both accumulator
+// kinds, tiles 32 x 8 -- three CTAs per SM -- and 32 x 16).
 #include "fused_stage.cuh"
 
 namespace sbli {

@@ -438,8 +438,9 @@ __device__ __forceinline__ void axis_terms_any(const LD& ldrec, const SF& sfun, 
 
 // TIN: type of the stage input in HBM; TOUT: type of the stage output.
 // CTAs per SM the launch bounds plan for: shared memory allows two 32 x 8
-// binary32 CTAs per SM (97.5 KiB each); binary64 (194.5 KiB) and 32 x 16
-// tiles take one.
+// binary32 CTAs per SM with the 5-slot ring (97.5 KiB each) and three with
+// the TMEM queue and 3-slot ring (64 KiB each, 80 registers); binary64 and
+// double-float (194.5 KiB) and 32 x 16 tiles take one.
 template <typename T, int TY, bool ZT = false>
 constexpr int fused_min_blocks() {
   return (sizeof(T) == 4 && TY <= 8) ? (ZT ? 3 : 2) : 1;
