@@ -366,6 +366,76 @@ def test_T7_initial_field_values(orc):
     assert np.max(np.abs(T - 1.0)) < 1e-13
 
 
+@pytest.mark.parametrize("A", [1.0, 0.7])
+def test_T7_initial_total_energy_and_pressure(orc, A):
+    """Mean total energy of the initial field is 1/(gamma (gamma-1) M^2) +
+    A^2/8 (the pressure fluctuation of Eq. 12 averages to zero on the grid,
+    the kinetic part is A^2/8), and the pressure recovered through Eq. 4 is
+    Eq. 12 at every point."""
+    p = orc.params(12)
+    q = orc.init_tgv(p, A)
+    want = 1.0 / (GAMMA * (GAMMA - 1.0) * MACH**2) + A * A / 8.0
+    assert float(np.mean(q[4])) == pytest.approx(want, rel=1e-14)
+    x, y, z = grid(p)
+    pr = 1 / (GAMMA * MACH**2) + A * A * (np.cos(2 * x) + np.cos(2 * y)) * (2 + np.cos(2 * z)) / 16
+    _, prim_p, _ = orc.primitives(p, q)
+    assert rel(prim_p, pr) < 1e-13
+
+
+@pytest.mark.parametrize("a", [0, 1, 2])
+def test_T7_enstrophy_of_a_shear_pair(orc, a):
+    """With axes (a, b, c) cyclic, u_b = -sin(x_b + x_c), u_c = sin(x_b + x_c)
+    and u_a = 0 is solenoidal and its only vorticity component is
+    omega_a = du_c/dx_b - du_b/dx_c = 2 cos(x_b + x_c); with Eq. 6 each
+    derivative carries s1(1), so at rho = 1 the enstrophy is s1(1)^2 and the
+    kinetic energy 1/2.  Both terms of omega_a are nonzero and equal, so a
+    sign slip inside the curl halves or cancels it (the Taylor-Green field,
+    with one nonzero term per component, cannot show that)."""
+    p = orc.params(10)
+    X = grid(p)
+    b, c = (a + 1) % 3, (a + 2) % 3
+    phase = X[b] + X[c] + np.zeros((10, 10, 10))
+    q = np.zeros((5, 10, 10, 10))
+    q[0] = 1.0
+    q[1 + b] = -np.sin(phase)
+    q[1 + c] = np.sin(phase)
+    q[4] = 1.0 / (GAMMA * (GAMMA - 1.0) * MACH**2) + 0.5 * (q[1 + b] ** 2 + q[1 + c] ** 2)
+    ke, ens = orc.ke_enstrophy(p, q)
+    assert ke == pytest.approx(0.5, rel=1e-14)
+    assert ens == pytest.approx(s1(1, orc.h(p, 0)) ** 2, rel=1e-13)
+
+
+@pytest.mark.parametrize("n", [(9, 10, 11), (12, 8, 10)])
+def test_T7_enstrophy_identity_random_field(orc, n):
+    """For any periodic velocity at rho = 1, sum |omega|^2 = sum |D u|^2 -
+    sum (D . u)^2 holds for the Eq. 6 operators exactly up to rounding:
+    the cross sum (D_j u_i)(D_i u_j) equals sum (D_i u_i)(D_j u_j) because
+    the periodic stencils commute and are skew-adjoint (summation by parts).
+    The right side uses only first derivatives, never the curl, so a sign or
+    index slip in any vorticity component breaks the identity."""
+    p = orc.params(n)
+    # the three components share their wavevectors (random amplitudes and
+    # phases each), so every cross product D_b u_c * D_c u_b has a nonzero sum
+    rng = np.random.default_rng(41)
+    X = grid(p)
+    q = np.zeros((5, n[2], n[1], n[0]))
+    q[0] = 1.0
+    q[4] = 180.0
+    for _ in range(8):
+        k = rng.integers(-3, 4, size=3)
+        if not k.any():
+            k[0] = 1
+        phase = k[0] * X[0] + k[1] * X[1] + k[2] * X[2]
+        for i in range(3):
+            q[1 + i] += rng.uniform(0.1, 0.3) * np.cos(phase + rng.uniform(0.0, 2.0 * math.pi))
+    _, ens = orc.ke_enstrophy(p, q)
+    du = [[orc.d1(p, np.ascontiguousarray(q[1 + i]), j) for j in range(3)] for i in range(3)]
+    grad2 = sum(float(np.mean(du[i][j] ** 2)) for i in range(3) for j in range(3))
+    div2 = float(np.mean((du[0][0] + du[1][1] + du[2][2]) ** 2))
+    assert 2.0 * ens == pytest.approx(grad2 - div2, rel=1e-12)
+    assert div2 > 0.1 * grad2  # the random field is not solenoidal: the identity is not trivial
+
+
 # ------------------------------------------------------- T8 viscous decay
 
 def test_T8_low_reynolds_kinetic_energy_decay(orc):
