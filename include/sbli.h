@@ -103,7 +103,9 @@ typedef struct sbli_grid sbli_grid;
 SBLI_API int sbli_abi_version(void);
 
 /* Bytes of device workspace a grid needs (state registers, stage fields and
- * scratch).  Returns SBLI_EINVAL for n_i < 5 or unknown precision/variant. */
+ * scratch).  Returns SBLI_EINVAL for n_i < 5, n0*n1 >= 2^31, n0*n1*n2 >= 2^32
+ * (the stage kernels address a point of one field with a 32-bit unsigned
+ * offset) or unknown precision/variant. */
 SBLI_API int sbli_workspace_bytes(int n0, int n1, int n2, int precision, int variant, size_t* bytes);
 
 /* Create a grid over a caller-owned device workspace of at least
@@ -129,6 +131,16 @@ SBLI_API int sbli_init_tgv(sbli_grid* g, double amplitude);
  * of a time step. */
 SBLI_API int sbli_set_state(sbli_grid* g, const double* q, int q_is_host);
 SBLI_API int sbli_get_state(sbli_grid* g, double* q, int q_is_host);
+
+/* Read a few points of the state without a full copy (grids too large for a
+ * second state-sized buffer).  idx_dev: count linear point indices
+ * i0 + n0*(i1 + n1*i2) in device memory (int64); out_dev: device memory for
+ * 5*count binary64, written field-major (out_dev[f*count + m] is field f of
+ * point idx_dev[m]) with the plain conserved variables, bit-identical to the
+ * same entries of sbli_get_state.  An index outside [0, n0*n1*n2) yields NaN
+ * in its five entries (no fault).  count == 0 is a no-op.  Asynchronous on
+ * the grid's stream; SBLI_EINVAL between the stages of a step. */
+SBLI_API int sbli_sample_state(sbli_grid* g, const long long* idx_dev, int count, double* out_dev);
 
 /* Between the stages of a step (after stage 0 or 1): copy out the next
  * stage's input field Q_k and the accumulator Q_acc as 5*n0*n1*n2 binary64

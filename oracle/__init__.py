@@ -81,6 +81,8 @@ def _load():
                 "orc_step": (None, [P, _DP, ctypes.c_double, ctypes.c_int]),
                 "orc_rk_coefficients": (None, [_DP, _DP]),
                 "orc_init_tgv": (None, [P, ctypes.c_double, _DP]),
+                "orc_init_tgv_window": (None, [P, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), _DP]),
                 "orc_ke_enstrophy": (None, [P, _DP, _DP, _DP]),
                 "orc_set_threads": (None, [ctypes.c_int]),
                 "orc_get_threads": (ctypes.c_int, []),
@@ -226,6 +228,25 @@ def init_tgv(p: Params, A: float = 1.0) -> np.ndarray:
     q = np.empty(shape(p, 5))
     _load().orc_init_tgv(ctypes.byref(p), float(A), _ptr(q))
     return q
+
+
+def init_tgv_window(p: Params, A: float, origin, width) -> np.ndarray:
+    """The TGV field of grid ``p`` on a window: shape (5, w2, w1, w0), first
+    point the global point ``origin`` (wrapped periodically)."""
+    o = (ctypes.c_int * 3)(*(int(v) for v in origin))
+    w = (ctypes.c_int * 3)(*(int(v) for v in width))
+    q = np.empty((5, int(width[2]), int(width[1]), int(width[0])))
+    _load().orc_init_tgv_window(ctypes.byref(p), float(A), o, w, _ptr(q))
+    return q
+
+
+def window_params(p: Params, width) -> Params:
+    """Params of a window grid with the same spacing h as ``p`` along each
+    axis (n = width, L scaled by width/n; the stencils see only h)."""
+    if p.n[0] != p.n[1] or p.n[1] != p.n[2] or width[0] != width[1] or width[1] != width[2]:
+        raise ValueError("window params need a cubic grid and a cubic window (one L for all axes)")
+    return params(tuple(int(v) for v in width), Re=p.Re, Mach=p.Mach, Pr=p.Pr, gamma=p.gamma,
+                  L=p.L * width[0] / p.n[0], energy_form=p.energy_form)
 
 
 def ke_enstrophy(p: Params, q: np.ndarray):

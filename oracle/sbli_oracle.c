@@ -454,30 +454,49 @@ void orc_step(const orc_params* p, double* q, double dt, int nsteps) {
 
 /* ------------------------------------------------- Taylor-Green field (§4) */
 
+/* Eqs. 9-12 at global point (i, j, k) with amplitude A (R5): rho, rho u_0..2, rho E */
+static void tgv_point(const orc_params* p, double A, int i, int j, int k, double out[5]) {
+  const double g = p->gamma, M = p->Mach, L = p->L;
+  /* R6: x = i h */
+  const double x = i * orc_h(p, 0), y = j * orc_h(p, 1), z = k * orc_h(p, 2);
+  const double u0 = A * sin(x / L) * cos(y / L) * cos(z / L);
+  const double u1 = -A * cos(x / L) * sin(y / L) * cos(z / L);
+  const double u2 = 0.0;
+  const double pr = 1.0 / (g * M * M) + A * A / 16.0 * (cos(2.0 * x / L) + cos(2.0 * y / L)) * (2.0 + cos(2.0 * z / L));
+  /* R4: T = 1, so rho = gamma M^2 p by Eq. 5 */
+  const double rho = g * M * M * pr;
+  /* Eq. 4 solved for rho E */
+  const double rhoE = pr / (g - 1.0) + 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2);
+  out[0] = rho;
+  out[1] = rho * u0;
+  out[2] = rho * u1;
+  out[3] = rho * u2;
+  out[4] = rhoE;
+}
+
 void orc_init_tgv(const orc_params* p, double A, double* q) {
   const size_t P = npoints(p);
-  const double g = p->gamma, M = p->Mach, L = p->L;
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < p->n[2]; ++k)
     for (int j = 0; j < p->n[1]; ++j)
       for (int i = 0; i < p->n[0]; ++i) {
-        /* R6: x = i h */
-        const double x = i * orc_h(p, 0), y = j * orc_h(p, 1), z = k * orc_h(p, 2);
-        /* Eqs. 9-12 with amplitude A (R5) */
-        const double u0 = A * sin(x / L) * cos(y / L) * cos(z / L);
-        const double u1 = -A * cos(x / L) * sin(y / L) * cos(z / L);
-        const double u2 = 0.0;
-        const double pr = 1.0 / (g * M * M) + A * A / 16.0 * (cos(2.0 * x / L) + cos(2.0 * y / L)) * (2.0 + cos(2.0 * z / L));
-        /* R4: T = 1, so rho = gamma M^2 p by Eq. 5 */
-        const double rho = g * M * M * pr;
-        /* Eq. 4 solved for rho E */
-        const double rhoE = pr / (g - 1.0) + 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2);
+        double v[5];
+        tgv_point(p, A, i, j, k, v);
         const size_t n = at(p, i, j, k);
-        q[n] = rho;
-        q[P + n] = rho * u0;
-        q[2 * P + n] = rho * u1;
-        q[3 * P + n] = rho * u2;
-        q[4 * P + n] = rhoE;
+        for (int f = 0; f < 5; ++f) q[(size_t)f * P + n] = v[f];
+      }
+}
+
+void orc_init_tgv_window(const orc_params* p, double A, const int origin[3], const int width[3], double* q) {
+  const size_t W = (size_t)width[0] * width[1] * width[2];
+  for (int c = 0; c < width[2]; ++c)
+    for (int b = 0; b < width[1]; ++b)
+      for (int a = 0; a < width[0]; ++a) {
+        double v[5];
+        /* the periodic image of the window point inside the grid */
+        tgv_point(p, A, wrap(origin[0] + a, p->n[0]), wrap(origin[1] + b, p->n[1]), wrap(origin[2] + c, p->n[2]), v);
+        const size_t n = (size_t)a + (size_t)width[0] * ((size_t)b + (size_t)width[1] * c);
+        for (int f = 0; f < 5; ++f) q[(size_t)f * W + n] = v[f];
       }
 }
 

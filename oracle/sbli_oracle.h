@@ -83,6 +83,15 @@ void orc_rk_coefficients(double a[3], double b[3]);
 /* Taylor-Green initial field of §4 with velocity amplitude A (A = 1 in the paper). */
 void orc_init_tgv(const orc_params* p, double A, double* q);
 
+/* The same field on a width[0] x width[1] x width[2] window of the grid p
+ * whose first point is the global point origin (wrapped periodically; the
+ * window may be wider than the grid), field-major with x0 fastest.  Each
+ * value is the one orc_init_tgv gives the same global point.  With params
+ * of n = width and L scaled by width/n, orc_step on the window reproduces
+ * the full grid's step at every window point farther than 4 points per
+ * stage from the window's edge (the reach of the residual, Eqs. 6-7). */
+void orc_init_tgv_window(const orc_params* p, double A, const int origin[3], const int width[3], double* q);
+
 /* Volume averages: ke = <rho |u|^2 / 2>, ens = <rho |omega|^2 / 2>, omega = curl u by Eq. 6. */
 void orc_ke_enstrophy(const orc_params* p, const double* q, double* ke, double* ens);
 

@@ -54,6 +54,8 @@ bool valid_sizes(int n0, int n1, int n2) {
   if (n0 < 5 || n1 < 5 || n2 < 5) return false;
   // in-plane offsets are 32-bit in the kernels; grid index fits 2^31 planes
   if ((long long)n0 * n1 >= (1LL << 31)) return false;
+  // the fused kernels address a point within one field with a 32-bit unsigned offset
+  if ((long long)n0 * n1 * n2 >= (1LL << 32)) return false;
   if (n0 > (1 << 24) || n1 > (1 << 24) || n2 > (1 << 24)) return false;
   return true;
 }
@@ -330,7 +332,7 @@ const char* sbli_last_error(void) { return g_last_error.c_str(); }
 
 int sbli_workspace_bytes(int n0, int n1, int n2, int precision, int variant, size_t* bytes) {
   if (!bytes) return fail(SBLI_EINVAL, "bytes is null");
-  if (!valid_sizes(n0, n1, n2)) return fail(SBLI_EINVAL, "grid %d x %d x %d: each edge must be >= 5 and n0*n1 < 2^31", n0, n1, n2);
+  if (!valid_sizes(n0, n1, n2)) return fail(SBLI_EINVAL, "grid %d x %d x %d: each edge must be >= 5, n0*n1 < 2^31 and n0*n1*n2 < 2^32", n0, n1, n2);
   if (precision < SBLI_FP64 || precision > SBLI_DF64) return fail(SBLI_EINVAL, "unknown precision %d", precision);
   if (variant < SBLI_FUSED || variant > SBLI_SN2) return fail(SBLI_EINVAL, "unknown variant %d", variant);
   if ((precision == SBLI_FP32_DF || precision == SBLI_DF64) && variant != SBLI_FUSED)
@@ -466,6 +468,19 @@ int sbli_get_state(sbli_grid* g, double* q, int q_is_host) {
   } else {
     SBLI_TRY(cudaMemcpyAsync(q, tmp, bytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync D2D");
   }
+  return SBLI_OK;
+}
+
+int sbli_sample_state(sbli_grid* g, const long long* idx_dev, int count, double* out_dev) {
+  if (int rc = check_grid(g)) return rc;
+  if (count < 0) return fail(SBLI_EINVAL, "count %d < 0", count);
+  if (count == 0) return SBLI_OK;
+  if (!idx_dev || !out_dev) return fail(SBLI_EINVAL, "idx_dev or out_dev is null");
+  if (g->next_stage != 0) return fail(SBLI_EINVAL, "sample_state between stages of a step (next stage %d)", g->next_stage);
+  const bool df = g->precision == SBLI_FP32_DF;
+  const double* q64 = df ? nullptr : g->reg64[g->state];
+  const float* qdf = df ? reinterpret_cast<const float*>(g->reg64[g->state]) : nullptr;
+  SBLI_TRY(launch_sample_state(g->geom.P, g->ref, q64, qdf, idx_dev, count, out_dev, g->stream), "sample_state launch");
   return SBLI_OK;
 }
 

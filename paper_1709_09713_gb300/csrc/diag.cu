@@ -141,6 +141,43 @@ cudaError_t launch_df_join(long long P, const RefState& r, const float* src, dou
   return cudaGetLastError();
 }
 
+// Plain conserved variables at listed points: out[f * count + i] for the
+// point of linear index idx[i] (x0 fastest).  The binary64 state (q64) or the
+// double-float state (qdf: hi fields, then lo fields) is in deviation form;
+// the sums are those of the full-grid conversions, so a sample equals the
+// corresponding entry of a full read-out bit for bit.  Indices outside
+// [0, P) yield NaN in all five fields.
+__global__ void sample_state_kernel(long long P, double rho0, double E0, const double* __restrict__ q64,
+                                    const float* __restrict__ qdf, const long long* __restrict__ idx, int count,
+                                    double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const long long n = idx[i];
+    const bool inside = n >= 0 && n < P;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      double v = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
+      if (inside) {
+        const long long m = (long long)f * P + n;
+        if (q64) {  // as offset_kernel
+          v = q64[m];
+          if (f == 0) v += rho0;
+          if (f == 4) v += E0;
+        } else {  // as df_join_kernel
+          v = ((double)qdf[m] + (double)qdf[m + 5 * P]) + (f == 0 ? rho0 : (f == 4 ? E0 : 0.0));
+        }
+      }
+      out[(long long)f * count + i] = v;
+    }
+  }
+}
+
+cudaError_t launch_sample_state(long long P, const RefState& r, const double* q64, const float* qdf,
+                                const long long* idx, int count, double* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  sample_state_kernel<<<grid_for(count, 256), 256, 0, s>>>(P, r.rho0, r.E0, q64, qdf, idx, count, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ KE
 constexpr int KE_BLOCK = 256;
 constexpr int KE_MAX_BLOCKS = 1024;

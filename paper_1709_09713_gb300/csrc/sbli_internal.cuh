@@ -119,6 +119,10 @@ cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_
 // zero RefState to stay in deviation form.
 cudaError_t launch_df_split(long long P, const RefState& r, const double* src, float* dst, cudaStream_t s);
 cudaError_t launch_df_join(long long P, const RefState& r, const float* src, double* dst, cudaStream_t s);
+// Gather the plain conserved variables of count points (q64: binary64 state,
+// or qdf: double-float state) into out[5][count]; NaN for indices outside [0, P).
+cudaError_t launch_sample_state(long long P, const RefState& r, const double* q64, const float* qdf,
+                                const long long* idx, int count, double* out, cudaStream_t s);
 // KE/enstrophy of a binary64 offset state: per-CTA partials into scratch,
 // then a fixed-order final sum into out[0..1].
 int ke_num_partials(const Geom& g);

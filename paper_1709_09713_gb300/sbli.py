@@ -59,6 +59,7 @@ SIGNATURES = {
     "sbli_init_tgv": (_c_int, [_vp, _c_double]),
     "sbli_set_state": (_c_int, [_vp, _vp, _c_int]),
     "sbli_get_state": (_c_int, [_vp, _vp, _c_int]),
+    "sbli_sample_state": (_c_int, [_vp, _vp, _c_int, _vp]),
     "sbli_get_stage": (_c_int, [_vp, _vp, _vp, _c_int]),
     "sbli_rhs": (_c_int, [_vp, _vp]),
     "sbli_rk_stage": (_c_int, [_vp, _c_int, _c_double]),
@@ -163,6 +164,10 @@ def sbli_set_state(h: int, q_ptr: int, q_is_host: bool) -> None:
 
 def sbli_get_state(h: int, q_ptr: int, q_is_host: bool) -> None:
     _check(lib().sbli_get_state(_vp(h), _vp(q_ptr), int(bool(q_is_host))))
+
+
+def sbli_sample_state(h: int, idx_ptr: int, count: int, out_ptr: int) -> None:
+    _check(lib().sbli_sample_state(_vp(h), _vp(idx_ptr), int(count), _vp(out_ptr)))
 
 
 def sbli_get_stage(h: int, q_stage_ptr: int, q_acc_ptr: int, q_is_host: bool) -> None:
@@ -514,6 +519,18 @@ class Grid:
             out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
         assert out.dtype == torch.float64 and out.is_contiguous() and tuple(out.shape) == self.shape
         sbli_get_state(self.handle, out.data_ptr(), not out.is_cuda)
+        return out
+
+    def sample_state(self, idx):
+        """Plain conserved variables at linear point indices ``idx`` (int64
+        device tensor, i0 + n0*(i1 + n1*i2)) as a (5, len(idx)) binary64
+        device tensor; NaN where an index is outside the grid."""
+        import torch
+
+        assert idx.dtype == torch.int64 and idx.is_cuda and idx.dim() == 1
+        idx = idx.contiguous()
+        out = torch.empty((5, idx.numel()), dtype=torch.float64, device=self.device)
+        sbli_sample_state(self.handle, idx.data_ptr(), idx.numel(), out.data_ptr())
         return out
 
     def rhs(self, out=None):

@@ -63,6 +63,24 @@ def test_rejects_grids_below_stencil_width(sbli, n):
     assert "5" in sbli.sbli_last_error()
 
 
+@pytest.mark.parametrize("n", [(65536, 32768, 8), (2048, 2048, 1024), (1625, 1625, 1627)])
+def test_rejects_grids_beyond_32_bit_offsets(sbli, n):
+    """n0*n1 >= 2^31 or n0*n1*n2 >= 2^32 would overflow the stage kernels'
+    32-bit point offsets; the largest grids that fit a GB300 (~1300^3 at 120
+    bytes per point) stay below both."""
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_workspace_bytes(*n, sbli.SBLI_FP64, sbli.SBLI_FUSED)
+    assert e.value.code == sbli.SBLI_EINVAL
+    assert "2^32" in sbli.sbli_last_error()
+
+
+def test_accepts_the_largest_grids_that_fit(sbli):
+    # 1296^3 (2.18e9 points, past 2^31) and 1625^3 (4.29e9, just below 2^32)
+    for n in (1296, 1625):
+        b = sbli.sbli_workspace_bytes(n, n, n, sbli.SBLI_FP64, sbli.SBLI_FUSED)
+        assert b >= 3 * 5 * n**3 * 8
+
+
 def test_rejects_unknown_modes(sbli):
     with pytest.raises(sbli.SbliError) as e:
         sbli.sbli_workspace_bytes(8, 8, 8, 7, sbli.SBLI_FUSED)
@@ -112,6 +130,7 @@ def test_null_arguments_are_errors(sbli):
     assert lib.sbli_workspace_bytes(8, 8, 8, 0, 0, None) == sbli.SBLI_EINVAL
     assert lib.sbli_create_grid(None, 8, 8, 8, 0, 0, None, None, 0, None) == sbli.SBLI_EINVAL
     assert lib.sbli_rk_stage(None, 0, 1e-3) == sbli.SBLI_EINVAL
+    assert lib.sbli_sample_state(None, None, 1, None) == sbli.SBLI_EINVAL
     assert lib.sbli_destroy_grid(None) == sbli.SBLI_OK
     h = ctypes.c_void_p()
     prm = sbli.params()

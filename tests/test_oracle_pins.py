@@ -580,3 +580,42 @@ def test_oracle_matches_its_golden_fixture(orc):
     for (i, j, k), want in pts:
         for f in range(5):
             assert q[f, k, j, i] == pytest.approx(want[f], rel=1e-13, abs=1e-15)
+
+
+# ------------------------------------------------- windows of large grids
+
+@pytest.mark.parametrize("origin,width", [((0, 0, 0), (12, 10, 9)), ((-3, 8, 7), (7, 6, 5)), ((5, -11, 20), (25, 4, 3))])
+def test_window_init_is_the_grid_init_on_the_window(orc, origin, width):
+    """Each window value is bitwise the full grid's value at the periodic image
+    of its global point (windows may wrap, start negative, or be wider than
+    the grid)."""
+    p = orc.params((12, 10, 9))
+    full = orc.init_tgv(p, 0.9)
+    win = orc.init_tgv_window(p, 0.9, origin, width)
+    ii = (origin[0] + np.arange(width[0])) % 12
+    jj = (origin[1] + np.arange(width[1])) % 10
+    kk = (origin[2] + np.arange(width[2])) % 9
+    want = full[:, kk[:, None, None], jj[None, :, None], ii[None, None, :]]
+    assert np.array_equal(win, want)
+
+
+def test_window_step_reproduces_the_grid_step_at_its_centre(orc):
+    """One step on a 25^3 window (reach 3 stages x 4 points = 12 each side)
+    with the grid's spacing gives the full grid's step at the window centre:
+    the dependency cone of the centre never meets the window's wrap.  Not
+    bitwise: the window's h = 2 pi (L w/n)/w may differ from 2 pi L/n in the
+    last bit."""
+    p = orc.params(20)
+    dt = 1e-3
+    full = orc.step(p, orc.init_tgv(p), dt, 1)
+    pw = orc.window_params(p, (25, 25, 25))
+    assert orc.h(pw, 0) == pytest.approx(orc.h(p, 0), rel=1e-15)
+    for c in [(0, 0, 0), (19, 3, 11), (7, 19, 19)]:
+        origin = tuple(v - 12 for v in c)
+        win = orc.step(pw, orc.init_tgv_window(p, 1.0, origin, (25, 25, 25)), dt, 1)
+        got = win[:, 12, 12, 12]
+        want = full[:, c[2], c[1], c[0]]
+        assert np.max(np.abs(got - want) / np.array([1.0, 1.0, 1.0, 1.0, 200.0])) < 1e-14, (c, got - want)
+    # an off-centre window point inside the reach of the wrap does differ
+    win = orc.step(pw, orc.init_tgv_window(p, 1.0, (-12, -12, -12), (25, 25, 25)), dt, 1)
+    assert np.max(np.abs(win[:, 12, 12, 1] - full[:, 0, 0, 9])) > 1e-8
