@@ -120,6 +120,8 @@ def test_1296_cubed_one_step_sampled(S, oracle_samples, precision, cfg, tol, inc
         torch.cuda.empty_cache()
     assert np.isfinite(s1).all()
     e0, e1 = rel(s0, q0), rel(s1, q1)
+    print(f"1296^3 precision {precision} config {config}: state {max(e1):.2e}, "
+          f"increment {max(rel(s1 - s0, q1 - q0)):.2e}")
     assert max(e0) <= 1e-14, e0  # the initial fields agree to rounding
     assert max(e1) <= tol, (config, e1)
     if inc_tol is not None:
