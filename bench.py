@@ -51,10 +51,10 @@ FP64_FLOP_PER_CLK_PER_SM = 4.0
 ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "df64": 400.0 / 3.0}
 # binary64 flop per point-stage the fused kernel executes (2 DFMA + DADD +
 # DMUL), counted by ncu on the three stages of a 256^3 step, mean (profiles/).
-FUSED_FP64_FLOP_PER_PT = 591.1
+FUSED_FP64_FLOP_PER_PT = 572.1
 # DRAM bytes per launch, mean over the three stages of a step, from the ncu
 # captures summarised in profiles/ (an entry is removed once its kernel changes)
-NCU_TRAFFIC = {("fp64", 256): 2.251e9}
+NCU_TRAFFIC = {("fp64", 256): 2.249e9}
 # thread instructions per point-stage of the double-float kernel (ncu,
 # smsp__inst_executed x 32 / points); its ceiling is one warp instruction per
 # clock per SM sub-partition

@@ -81,16 +81,25 @@ struct FusedSmem {
   uint32_t tmem_base;         // TMEM allocation (z queue variant)
 };
 
+// 1/rho for the primitives (Eqs. 4-5): correctly rounded in binary64 and
+// double-float; binary32 takes the hardware approximation (rcp.approx,
+// within one unit in the last place), far inside the binary32 tolerance and
+// one instruction instead of the rounding-correction sequence.
+__device__ __forceinline__ float rcp_approx_f32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 template <typename T>
-__device__ __forceinline__ T rcp_rn(T x);
+__device__ __forceinline__ T recip(T x);
 template <>
-__device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
 template <>
-__device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip<float>(float x) { return rcp_approx_f32(x); }
 template <>
-__device__ __forceinline__ dfloat rcp_rn<dfloat>(dfloat x) { return dw_reciprocal(x); }
+__device__ __forceinline__ dfloat recip<dfloat>(dfloat x) { return dw_reciprocal(x); }
 template <>
-__device__ __forceinline__ f32x2 rcp_rn<f32x2>(f32x2 x) { return f32x2(__frcp_rn(x.x), __frcp_rn(x.y)); }
+__device__ __forceinline__ f32x2 recip<f32x2>(f32x2 x) { return f32x2(rcp_approx_f32(x.x), rcp_approx_f32(x.y)); }
 
 // Record load/store with 8-byte (binary32: 40-byte records) or 16-byte
 // (binary64: 80-byte records) vector accesses; both strides are bank-conflict
@@ -383,7 +392,8 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
                                                   const T (&uc)[3], Terms<T>& t) {
   const T c1 = c.c1[A], c2 = c.c2[A], e1 = c.e1[A], e2 = c.e2[A];
   const T ua = uc[A];
-  T gA = T(0);                        // sum_k (e_k u_A,k + c_k s_k): G_A without its centre term
+  T lAA = T(0);                       // sum_k e_k u_A,k: D2_A u_A without its centre term
+  T gA = T(0);                        // sum_k c_k s_k = D1_A s_A
   T gI[3] = {T(0), T(0), T(0)};      // D1_A u_i, i != A
   // binary64 (bound by its FMA pipe): the per-axis products c u_A^c and the
   // doubled weights 2c once, so each neighbour's weights are one FMA / one
@@ -414,17 +424,21 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
     t.rE = mad(w, r[V_E], mad(x2, r[V_P], t.rE));
     t.rrho = mad(cd, fma(ua, r[V_RHO], r[V_M0 + A]), t.rrho);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) t.lap[i] = mad(ed, r[V_U0 + i], t.lap[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      if (i != A) gI[i] = mad(cd, r[V_U0 + i], gI[i]);
-    gA = mad(ed, r[V_U0 + A], mad(cd, sk, gA));
+    for (int i = 0; i < 3; ++i) {
+      if (i != A) {
+        t.lap[i] = mad(ed, r[V_U0 + i], t.lap[i]);
+        gI[i] = mad(cd, r[V_U0 + i], gI[i]);
+      }
+    }
+    lAA = mad(ed, r[V_U0 + A], lAA);  // shared by the Laplacian of u_A and G_A
+    gA = mad(cd, sk, gA);
     t.lapT = mad(ed, r[V_T], t.lapT);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     if (i != A) t.g[i][A] = gI[i];
-  t.G[A] = fma(c.e0[A], uc[A], gA);
+  t.lap[A] += lAA;
+  t.G[A] = fma(c.e0[A], uc[A], lAA + gA);  // D2_A u_A + D1_A s_A (Eq. 7 on j = A, D1 o D1 otherwise)
 }
 
 template <int A, typename T, typename LD, typename SF>
@@ -618,7 +632,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           const T m1 = from_lanes<T, TIN>(pf[l][2]);
           const T m2 = from_lanes<T, TIN>(pf[l][3]);
           const T E_p = from_lanes<T, TIN>(pf[l][4]);
-          const T rinv = rcp_rn<T>(T(1) + rho_p);
+          const T rinv = recip<T>(T(1) + rho_p);
           const T u0 = m0 * rinv, u1 = m1 * rinv, u2 = m2 * rinv;
           const T mu = mad(m2, u2, mad(m1, u1, m0 * u0));
           const T p_p = c.gm1 * mad(T(-0.5), mu, E_p);    // Eq. 4: p - p_ref
