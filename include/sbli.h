@@ -207,7 +207,8 @@ SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, in
  * binary32 paths, where each thread keeps its column's records of the five
  * x2 planes (z_queue = 0: the shared-memory ring; 1: a per-thread queue in
  * Blackwell tensor memory, with only three full-record planes in shared
- * memory) and how many columns each thread owns (columns_per_thread = 1, or
+ * memory at tile_y 8, four at 16, which saves one barrier per plane) and
+ * how many columns each thread owns (columns_per_thread = 1, or
  * 2: columns x and x + 32 of a 64 x 8 tile computed together in packed
  * two-lane FP32 instructions; shared-memory ring only).  Tile height, planes
  * per CTA and z_queue give bitwise the same state; two columns per thread

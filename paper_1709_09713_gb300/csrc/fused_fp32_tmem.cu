@@ -1,7 +1,8 @@
 // fused_fp32_tmem.cu -- binary32 stage kernels whose x2-neighbour records
 // come from a per-thread queue in tensor memory instead of the shared-memory
-// ring, with three full-record planes in shared memory (both accumulator
-// kinds, tiles 32 x 8 -- three CTAs per SM -- and 32 x 16).
+// ring (both accumulator kinds): tiles 32 x 8 with three full-record planes
+// in shared memory (three CTAs per SM) and 32 x 16 with four (two barriers
+// per plane).
 #include "fused_stage.cuh"
 
 namespace sbli {

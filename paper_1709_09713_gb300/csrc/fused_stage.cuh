@@ -27,7 +27,11 @@
 //     ring planes, and their D1_x u0 / D1_y u1, in tensor memory (TMEM), so
 //     the x2 derivatives read TMEM and shared memory keeps full records only
 //     for the entering, middle and centre planes, plus u_2 of the five planes
-//     for D1_z u_2 on the halo: 64 KiB per 32 x 8 CTA, three CTAs per SM;
+//     for D1_z u_2 on the halo: 64 KiB per 32 x 8 CTA, three CTAs per SM.
+//     32 x 16 tiles (one CTA per SM) keep a fourth full-record plane (the one
+//     that was the centre one plane earlier): the next entering plane then
+//     overwrites a slot nobody reads any more, so the barrier that ends each
+//     plane is not needed (two barriers per plane instead of three);
 //   * the arithmetic type T is double, float, dfloat (double-float, binary64
 //     storage) or f32x2 (two columns per thread in packed FP32x2 instructions);
 //   * the mixed second derivatives of the stress divergence use, for each i,
@@ -66,10 +70,14 @@ enum { V_RHO, V_M0, V_M1, V_M2, V_E, V_U0, V_U1, V_U2, V_P, V_T, NV };
 // for the planes that are still to become the centre (entering, middle,
 // centre: 3 slots), u_2 alone on the five ring planes (for D1_z u_2 on the
 // halo), and no D1_x u0 / D1_y u1 ring.
+template <int TY, bool ZT>
+constexpr int full_slots() {
+  return ZT ? (TY >= 16 ? 4 : 3) : NSLOT;
+}
 template <typename T, int TY, bool ZT = false>
 struct FusedSmem {
   static constexpr int SY = TY + 2 * HALO;
-  static constexpr int NFULL = ZT ? 3 : NSLOT;
+  static constexpr int NFULL = full_slots<TY, ZT>();
   T ring[NFULL][SY][SX][NV];  // rho', m_i, E', u_i, p', T' per haloed point
   union {
     T u2ring[NSLOT][SY][SX];    // ZT: u_2 per haloed point of the five ring planes
@@ -174,9 +182,13 @@ constexpr int TM_TAIL = 8 * NSLOT;           // fields 8-9 of slot s: columns TM
 constexpr int TM_DIAG = TM_TAIL + 2 * NSLOT;  // D1_x u0, D1_y u1 of slot s: columns TM_DIAG + 2s, +1
 static_assert(NV == 10 && TM_DIAG + 2 * NSLOT <= TM_COLS_PER_WARP, "z queue must fit the warp's TMEM window");
 
+// columns a CTA of NW warps allocates: a power of two, at least 32
 template <int NW>
 constexpr int tmem_columns() {
-  return TM_COLS_PER_WARP * ((NW + 3) / 4) < 32 ? 32 : TM_COLS_PER_WARP * ((NW + 3) / 4);
+  constexpr int need = TM_COLS_PER_WARP * ((NW + 3) / 4);
+  int c = 32;
+  while (c < need) c *= 2;
+  return c;
 }
 
 // win: this thread's window address (lane and window column), slot: ring slot
@@ -237,9 +249,9 @@ __device__ __forceinline__ void tmem_load_rec(uint32_t, int, f32x2 (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const f32x2 (&)[NV]) {}
 
 // Allocate / release the CTA's TMEM columns (warp 0), publishing the base
-// address through shared memory.  The column budget per SM (at most 256 with
-// these kernels' shared-memory footprints) is below the 512 available, so the
-// allocation never waits.
+// address through shared memory.  The CTAs that shared memory lets share an
+// SM never ask for more than the 512 columns available (32 x 8: 3 x 128;
+// 32 x 16: 256), so the allocation never waits.
 template <int NCOL>
 __device__ __forceinline__ uint32_t tmem_acquire(uint32_t* smem_slot) {
   if ((threadIdx.x >> 5) == 0) {
@@ -583,8 +595,13 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   int rs[NSLOT];
 #pragma unroll
   for (int k = 0; k < NSLOT; ++k) rs[k] = (k + 1) % NSLOT;  // any permutation; warm-up fills all slots
-  // full-record slots of planes e-2, e-1, e (ZT; otherwise the ring slots)
-  int rf[3] = {1, 2, 0};
+  // full-record slots (ZT; otherwise the ring slots): planes e-2, e-1, e, and
+  // e-3 in front of them when there are four
+  constexpr int NFULL = S::NFULL;
+  constexpr bool LAST_BARRIER = !ZT || NFULL < 4;  // the barrier that ends each plane
+  int rf[ZT ? NFULL : 1];
+#pragma unroll
+  for (int k = 0; k < (ZT ? NFULL : 1); ++k) rf[k] = (k + 1) % (ZT ? NFULL : 1);
 
   TIN pf[LPT][NF][PP];
   auto issue_loads = [&](int it_load) {
@@ -616,11 +633,11 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     const int se = rs[NSLOT - 1];
     if constexpr (ZT) {
       const int t0 = rf[0];
-      rf[0] = rf[1];
-      rf[1] = rf[2];
-      rf[2] = t0;
+#pragma unroll
+      for (int k = 0; k < NFULL - 1; ++k) rf[k] = rf[k + 1];
+      rf[NFULL - 1] = t0;
     }
-    const int fe = ZT ? rf[2] : se;  // full-record slot of the entering plane
+    const int fe = ZT ? rf[ZT ? NFULL - 1 : 0] : se;  // full-record slot of the entering plane
     {
       T* ring = &sm.ring[fe][0][0][0];
 #pragma unroll
@@ -680,7 +697,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     // slot of plane zc + o, o = -2..2
     const int sl[5] = {rs[0], rs[1], rs[2], rs[3], rs[4]};
     const int scen = sl[2];
-    const int fc = ZT ? rf[0] : scen;  // full-record slot of the centre plane
+    const int fc = ZT ? rf[ZT ? NFULL - 3 : 0] : scen;  // full-record slot of the centre plane
     unsigned oc[PP];  // offsets of the thread's centre points
 #pragma unroll
     for (int j = 0; j < PP; ++j) oc[j] = (unsigned)zc * plane + own[j];
@@ -893,8 +910,11 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         }
       }
     }
-    __syncthreads();
+    // with four full-record slots the next plane writes the slot of plane
+    // e-3, last read before this plane's first barrier
+    if constexpr (LAST_BARRIER) __syncthreads();
   }
+  if constexpr (!LAST_BARRIER) __syncthreads();  // the caller may reuse shared memory
 }
 
 // Fixed-order block reduction of (ke, ens) into out[0..1]: warp shuffles,

@@ -272,8 +272,9 @@ def test_error_paths_fault_nothing(S):
     "precision,configs",
     [
         (1, [(8, 4, 0, 1), (8, 13, 0, 1), (16, 7, 0, 1), (16, 40, 0, 1), (8, 13, 1, 1), (16, 7, 1, 1),
-             (16, 40, 1, 1), (8, 4, 1, 1), (8, 4, 0, 2), (8, 13, 0, 2), (8, 40, 0, 2)]),
-        (2, [(8, 4, 0, 1), (16, 7, 0, 1), (8, 13, 1, 1), (16, 40, 1, 1), (8, 5, 0, 2), (8, 40, 0, 2)]),
+             (16, 40, 1, 1), (8, 4, 1, 1), (16, 4, 1, 1), (8, 4, 0, 2), (8, 13, 0, 2), (8, 40, 0, 2)]),
+        (2, [(8, 4, 0, 1), (16, 7, 0, 1), (8, 13, 1, 1), (16, 40, 1, 1), (16, 5, 1, 1), (8, 5, 0, 2),
+             (8, 40, 0, 2)]),
         (0, [(8, 4, 0, 1), (8, 9, 0, 1), (8, 40, 0, 1)]),
         (3, [(8, 4, 0, 1), (8, 40, 0, 1)]),
     ],
@@ -281,8 +282,9 @@ def test_error_paths_fault_nothing(S):
 @pytest.mark.parametrize("n", [(64, 48, 40), (96, 20, 12), (40, 9, 7)])
 def test_launch_configs_are_bitwise_identical(S, precision, configs, n):
     """Tile height, planes per CTA and where the x2-neighbour records live
-    (shared-memory ring or TMEM queue) change only the work decomposition and
-    data movement: every point's arithmetic is the same, so the state (and
+    (shared-memory ring or TMEM queue; 32 x 16 queue tiles with four
+    full-record planes and two barriers per plane) change only the work
+    decomposition and data movement: every point's arithmetic is the same, so the state (and
     the kinetic-energy history up to the order of its sums) is bitwise equal.
     Two columns per thread use packed two-lane instructions with their own
     multiply-add fusion: bitwise equal among themselves, within the binary32
@@ -341,6 +343,8 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     g.step_n(1, 1e-3)
     with pytest.raises(S.SbliError):
         g.set_config(12, 8)
+    with pytest.raises(S.SbliError):
+        g.set_config(12, 8, 1)
     with pytest.raises(S.SbliError):
         g.set_config(8, 8, 2)
     d = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
