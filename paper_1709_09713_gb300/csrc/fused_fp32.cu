@@ -57,9 +57,4 @@ int fused_num_ctas(const Geom& g, const FusedConfig& cfg) {
   return (int)(gx * gy * gz);
 }
 
-size_t fused_smem_bytes(int elem_bytes, int ty) {
-  if (elem_bytes == 8) return sizeof(FusedSmem<double, 8>);
-  return ty == 16 ? sizeof(FusedSmem<float, 16>) : sizeof(FusedSmem<float, 8>);
-}
-
 }  // namespace sbli

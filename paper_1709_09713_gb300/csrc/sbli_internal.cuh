@@ -104,7 +104,6 @@ cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& c, con
 cudaError_t launch_fused_fp32_tmem(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                                    bool df, bool rhs_only, cudaStream_t s);
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg);
-size_t fused_smem_bytes(int elem_bytes, int ty);
 
 // Diagnostics and state conversion (diag.cu).
 cudaError_t launch_init_tgv(const Geom& g, const sbli_params& p, double amplitude, double* q, cudaStream_t s);

@@ -139,3 +139,14 @@ def test_null_arguments_are_errors(sbli):
     bad = sbli.params(Re=-1.0)
     assert lib.sbli_create_grid(ctypes.byref(h), 8, 8, 8, 0, 0, ctypes.byref(bad), None, 0, None) == sbli.SBLI_EINVAL
     assert "param" in sbli.sbli_last_error()
+
+
+def test_missing_library_fails_loudly(sbli, monkeypatch):
+    """Without the compiled library every entry point raises: there is no
+    CPU fallback behind the binding."""
+    monkeypatch.setattr(sbli, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libsbli.so"))
+    monkeypatch.setattr(sbli, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        sbli.lib()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        sbli.sbli_workspace_bytes(16, 16, 16, sbli.SBLI_FP64, sbli.SBLI_FUSED)
