@@ -281,7 +281,26 @@ def time_steps(S, g, stream, steps, dt, ws):
     return dist_max(e0.elapsed_time(e1))
 
 
-def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709):
+def energy_per_pt_stage(g, stream, points, stage_ms, dt, nvml, seconds=1.0):
+    """NVML total-energy delta per point-stage over about `seconds` of
+    further steps (long enough for the counter's resolution), or None."""
+    import torch
+
+    if nvml is None or not nvml.ok:
+        return None
+    steps = max(1, int(seconds * 1e3 / (3.0 * stage_ms)))
+    torch.cuda.synchronize()
+    e0 = nvml.energy_mj()
+    g.step_n(steps, dt)
+    stream.synchronize()
+    e1 = nvml.energy_mj()
+    if e0 is None or e1 is None:
+        return None
+    return {"j_per_pt_stage": (e1 - e0) / 1e3 / (3.0 * points * steps), "steps": steps,
+            "source": "nvmlDeviceGetTotalEnergyConsumption delta over further steps after the timed ones"}
+
+
+def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None):
     """64 Taylor-Green members, N uniform over {32,48,64,96,128}, Re ~ U[100,1600],
     M ~ U[0.1,0.4], amplitude ~ U(0.9,1.1); binary32 stages with a binary64
     accumulator; one persistent launch per stage, graph-captured steps."""
@@ -306,13 +325,14 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709):
     ms = e0.elapsed_time(e1)
     pts = sum(m.n**3 for m in members)
     items = b.work_items()
+    energy = energy_per_pt_stage(b, stream, pts, ms / (3 * steps), dt, nvml)
     b.close()
     del b
     torch.cuda.empty_cache()
     return {"workload": f"ensemble of {count} TGV grids (N in {{32,48,64,96,128}}, Re U[100,1600], M U[0.1,0.4]), "
                         "fp32 + f64 accumulator, persistent launch per stage", "value": 3.0 * pts * steps * ws / (ms / 1e3),
             "unit": "pt-stage/s", "steps": steps, "points": pts, "work_items_per_stage": items,
-            "stage_ms": ms / (3 * steps), "launches_per_stage": 1}
+            "stage_ms": ms / (3 * steps), "launches_per_stage": 1, "energy": energy}
 
 
 def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, arena_gb=200.0, fp64_as=0):
@@ -369,7 +389,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2, "df64": 3}
 VARIANTS = {"fused": 0, "store_all": 1, "RS": 2, "SS": 3, "RA": 4, "SN": 5, "SN2": 6}
 
 
-def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=None):
+def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=None, nvml=None):
     """Throughput of one extra configuration (no e2e, no clocks)."""
     import torch
 
@@ -383,14 +403,15 @@ def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=N
     with torch.cuda.stream(stream):
         g.step_n(warmup, dt)
     ms = time_steps(S, g, stream, steps, dt, ws)
+    P = n**3
+    stage_ms = ms / (3 * steps)
+    energy = energy_per_pt_stage(g, stream, P, stage_ms, dt, nvml)
     g.close()
     del g
     torch.cuda.empty_cache()
-    P = n**3
-    stage_ms = ms / (3 * steps)
     out = {"workload": f"TGV {n}^3 {precision} {variant}", "value": 3.0 * P * steps * ws / (ms / 1e3),
            "unit": "pt-stage/s", "steps": steps, "stage_ms": stage_ms, "tile_y_planes": cfg,
-           "autotuned": bool(tune)}
+           "autotuned": bool(tune), "energy": energy}
     if variant == "fused":
         peaks, kind = measured_peaks()
         ach = ALG_BYTES[precision] * P / (stage_ms / 1e3) / 1e9
@@ -563,11 +584,11 @@ def run_ours(args):
                           "source": "nvmlDeviceGetTotalEnergyConsumption delta over the timed region"}
     if not args.no_legs:
         cg = (clk.get("sm_mhz") or 2070.0) / 1e3
-        line["legs"] = [leg(S, 256, "df64", "fused", args.leg_steps, 2, dt, ws, clock_ghz=cg),
-                        leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
-                        leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True),
+        line["legs"] = [leg(S, 256, "df64", "fused", args.leg_steps, 2, dt, ws, clock_ghz=cg, nvml=nvml),
+                        leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
+                        leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
                         algorithms_leg(S, 256, args.alg_steps, 1, dt, ws, nvml),
-                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws),
+                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws, nvml=nvml),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
                                     fp64_as=S.SBLI_DF64)]
