@@ -202,15 +202,16 @@ SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, in
                                          void* stream);
 
 /* Launch configuration of the fused kernel: in-plane tile height (the tile
- * is 32 x tile_y points per column a thread owns; binary64 grids use 8,
- * binary32 grids 8 or 16), planes per CTA along x2 (>= 4) and, for the
- * binary32 paths, where each thread keeps its column's records of the five
+ * is 32 x tile_y points per column a thread owns; binary64-register grids
+ * (SBLI_FP64, SBLI_DF64) use 8, binary32 grids 8 or 16), planes per CTA
+ * along x2 (>= 4), where each thread keeps its column's records of the five
  * x2 planes (z_queue = 0: the shared-memory ring; 1: a per-thread queue in
  * Blackwell tensor memory, with only three full-record planes in shared
- * memory at tile_y 8, four at 16, which saves one barrier per plane) and
- * how many columns each thread owns (columns_per_thread = 1, or
- * 2: columns x and x + 32 of a 64 x 8 tile computed together in packed
- * two-lane FP32 instructions; shared-memory ring only).  Tile height, planes
+ * memory -- four for binary32 tile_y 16, which saves one barrier per plane)
+ * and, for binary32 grids, how many columns each thread owns
+ * (columns_per_thread = 1, or 2: columns x and x + 32 of a 64 x 8 tile
+ * computed together in packed two-lane FP32 instructions; shared-memory
+ * ring only).  Tile height, planes
  * per CTA and z_queue give bitwise the same state; two columns per thread
  * fuse multiply-adds differently (bitwise equal among themselves, within the
  * binary32 tolerance of one column).  set_config validates and applies it

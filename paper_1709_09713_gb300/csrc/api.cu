@@ -174,7 +174,7 @@ FusedConfig default_config(const Geom& g, int precision) {
 
 bool valid_config(int precision, int ty, int zc, int zq = 0, int px = 1) {
   if (zc < 4 || zq < 0 || zq > 1 || px < 1 || px > 2) return false;
-  if (f64_registers(precision)) return ty == 8 && zq == 0 && px == 1;
+  if (f64_registers(precision)) return ty == 8 && px == 1;  // shared-memory ring or TMEM queue
   if (px == 2) return ty == 8 && zq == 0;  // 64 x 8 two-column tiles, shared-memory ring
   return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
 }

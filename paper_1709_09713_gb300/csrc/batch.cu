@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     batch_stage_kernel(const __grid_constant__ BatchParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, TY, ZT>& sm = *reinterpret_cast<FusedSmem<T, TY, ZT>*>(smem_raw);
-  constexpr int NCOL = tmem_columns<TY>();
+  constexpr int NCOL = tmem_columns<TY, T>();
   uint32_t tbase = 0;
   if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
   for (long long item = blockIdx.x; item < p.total_items; item += gridDim.x) {

@@ -7,17 +7,18 @@
 
 namespace sbli {
 
-template <int TY>
+template <int TY, bool ZT>
 static cudaError_t dispatch_df64(const StageArgs& a, const Coef<dfloat>& c, bool rhs_only, cudaStream_t s) {
-  if (rhs_only) return launch_fused_t<dfloat, double, double, TY, true, false>(a, c, s);
-  if (a.ke_partials) return launch_fused_t<dfloat, double, double, TY, false, true>(a, c, s);
-  return launch_fused_t<dfloat, double, double, TY, false, false>(a, c, s);
+  if (rhs_only) return launch_fused_t<dfloat, double, double, TY, true, false, false, ZT>(a, c, s);
+  if (a.ke_partials) return launch_fused_t<dfloat, double, double, TY, false, true, false, ZT>(a, c, s);
+  return launch_fused_t<dfloat, double, double, TY, false, false, false, ZT>(a, c, s);
 }
 
 cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
                               cudaStream_t s) {
   switch (cfg.ty) {
-    case 8: return dispatch_df64<8>(a, c, rhs_only, s);
+    case 8:
+      return cfg.zq ? dispatch_df64<8, true>(a, c, rhs_only, s) : dispatch_df64<8, false>(a, c, rhs_only, s);
     default: return cudaErrorInvalidValue;
   }
 }

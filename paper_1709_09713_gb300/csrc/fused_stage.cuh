@@ -173,19 +173,27 @@ __device__ __forceinline__ void store_rec(dfloat* p, const dfloat (&r)[NV]) {
 
 // ---- tensor memory (TMEM) as a per-thread queue of x2-neighbour records.
 // Each warp of the CTA owns the 32 TMEM lanes of its quarter (warp % 4) and a
-// 64-column window (warp / 4); a thread keeps its own column's records of the
-// five ring planes there: fields 0-7 of slot s in columns 8s .. 8s+7, fields
-// 8-9 in columns 40+2s, 41+2s, so every access is aligned to its own width.
-// 32x32b shapes: each thread of the warp reads or writes its own lane.
-constexpr int TM_COLS_PER_WARP = 64;
-constexpr int TM_TAIL = 8 * NSLOT;           // fields 8-9 of slot s: columns TM_TAIL + 2s, +1
-constexpr int TM_DIAG = TM_TAIL + 2 * NSLOT;  // D1_x u0, D1_y u1 of slot s: columns TM_DIAG + 2s, +1
-static_assert(NV == 10 && TM_DIAG + 2 * NSLOT <= TM_COLS_PER_WARP, "z queue must fit the warp's TMEM window");
+// column window (warp / 4); a thread keeps its own column's records of the
+// five ring planes there.  A value takes W 32-bit columns (binary32: 1;
+// binary64 and double-float: 2): fields 0-7 of slot s in columns 8W s ..
+// 8W s + 8W - 1, fields 8-9 from column 40W + 2W s, and the pair
+// (D1_x u0, D1_y u1) from column 50W + 2W s, so every access is aligned to
+// its own width; windows are 64 W columns.  32x32b shapes: each thread of
+// the warp reads or writes its own lane.
+template <typename T>
+struct TmLayout {
+  static constexpr int W = sizeof(T) / 4;      // 32-bit columns per value
+  static constexpr int HEAD = 8 * W;           // columns of fields 0-7 of one slot
+  static constexpr int TAIL = HEAD * NSLOT;    // fields 8-9 of slot s: columns TAIL + 2W s ...
+  static constexpr int DIAG = TAIL + 2 * W * NSLOT;  // D1_x u0, D1_y u1 of slot s: DIAG + 2W s ...
+  static constexpr int COLS = 64 * W;          // window width
+  static_assert(NV == 10 && DIAG + 2 * W * NSLOT <= COLS, "z queue must fit the warp's TMEM window");
+};
 
 // columns a CTA of NW warps allocates: a power of two, at least 32
-template <int NW>
+template <int NW, typename T = float>
 constexpr int tmem_columns() {
-  constexpr int need = TM_COLS_PER_WARP * ((NW + 3) / 4);
+  constexpr int need = TmLayout<T>::COLS * ((NW + 3) / 4);
   int c = 32;
   while (c < need) c *= 2;
   return c;
@@ -193,7 +201,8 @@ constexpr int tmem_columns() {
 
 // win: this thread's window address (lane and window column), slot: ring slot
 __device__ __forceinline__ void tmem_store_rec(uint32_t win, int slot, const float (&r)[NV]) {
-  const uint32_t taddr = win + (uint32_t)(8 * slot), ttail = win + (uint32_t)(TM_TAIL + 2 * slot);
+  using L = TmLayout<float>;
+  const uint32_t taddr = win + (uint32_t)(L::HEAD * slot), ttail = win + (uint32_t)(L::TAIL + 2 * slot);
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
       "tcgen05.st.sync.aligned.32x32b.x2.b32 [%9], {%10, %11};\n\t"
@@ -205,7 +214,8 @@ __device__ __forceinline__ void tmem_store_rec(uint32_t win, int slot, const flo
 }
 
 __device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, float (&r)[NV]) {
-  const uint32_t taddr = win + (uint32_t)(8 * slot), ttail = win + (uint32_t)(TM_TAIL + 2 * slot);
+  using L = TmLayout<float>;
+  const uint32_t taddr = win + (uint32_t)(L::HEAD * slot), ttail = win + (uint32_t)(L::TAIL + 2 * slot);
   uint32_t v[NV];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%10];\n\t"
@@ -222,7 +232,7 @@ __device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, float (&r)
 __device__ __forceinline__ void tmem_store_diag(uint32_t win, int slot, float d00, float d11) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n\t"
-      "tcgen05.wait::st.sync.aligned;" ::"r"(win + (uint32_t)(TM_DIAG + 2 * slot)),
+      "tcgen05.wait::st.sync.aligned;" ::"r"(win + (uint32_t)(TmLayout<float>::DIAG + 2 * slot)),
       "r"(__float_as_uint(d00)), "r"(__float_as_uint(d11))
       : "memory");
 }
@@ -232,26 +242,118 @@ __device__ __forceinline__ void tmem_load_diag(uint32_t win, int slot, float& d0
       "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
       : "=r"(a), "=r"(b)
-      : "r"(win + (uint32_t)(TM_DIAG + 2 * slot))
+      : "r"(win + (uint32_t)(TmLayout<float>::DIAG + 2 * slot))
       : "memory");
   d00 = __uint_as_float(a);
   d11 = __uint_as_float(b);
 }
+
+// 8-byte values as two 32-bit words: binary64 (low, high word), double-float (hi, lo)
+__device__ __forceinline__ void to_words(double x, uint32_t& a, uint32_t& b) {
+  a = (uint32_t)__double2loint(x);
+  b = (uint32_t)__double2hiint(x);
+}
+__device__ __forceinline__ void from_words(uint32_t a, uint32_t b, double& x) {
+  x = __hiloint2double((int)b, (int)a);
+}
+__device__ __forceinline__ void to_words(dfloat x, uint32_t& a, uint32_t& b) {
+  a = __float_as_uint(x.hi);
+  b = __float_as_uint(x.lo);
+}
+__device__ __forceinline__ void from_words(uint32_t a, uint32_t b, dfloat& x) {
+  x.hi = __uint_as_float(a);
+  x.lo = __uint_as_float(b);
+}
+
 template <typename T>
-__device__ __forceinline__ void tmem_store_diag(uint32_t, int, T, T) {}
+__device__ __forceinline__ void tmem_store_rec8(uint32_t win, int slot, const T (&r)[NV]) {
+  using L = TmLayout<T>;
+  const uint32_t taddr = win + (uint32_t)(L::HEAD * slot), ttail = win + (uint32_t)(L::TAIL + 4 * slot);
+  uint32_t w[2 * NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) to_words(r[i], w[2 * i], w[2 * i + 1]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%17], {%18, %19, %20, %21};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]),
+      "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15]), "r"(ttail), "r"(w[16]), "r"(w[17]),
+      "r"(w[18]), "r"(w[19])
+      : "memory");
+}
 template <typename T>
-__device__ __forceinline__ void tmem_load_diag(uint32_t, int, T&, T&) {}
-__device__ __forceinline__ void tmem_load_rec(uint32_t, int, double (&)[NV]) {}
-__device__ __forceinline__ void tmem_store_rec(uint32_t, int, const double (&)[NV]) {}
-__device__ __forceinline__ void tmem_load_rec(uint32_t, int, dfloat (&)[NV]) {}
-__device__ __forceinline__ void tmem_store_rec(uint32_t, int, const dfloat (&)[NV]) {}
+__device__ __forceinline__ void tmem_load_rec8(uint32_t win, int slot, T (&r)[NV]) {
+  using L = TmLayout<T>;
+  const uint32_t taddr = win + (uint32_t)(L::HEAD * slot), ttail = win + (uint32_t)(L::TAIL + 4 * slot);
+  uint32_t w[2 * NV];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%20];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%21];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]), "=r"(w[8]),
+        "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15]), "=r"(w[16]),
+        "=r"(w[17]), "=r"(w[18]), "=r"(w[19])
+      : "r"(taddr), "r"(ttail)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < NV; ++i) from_words(w[2 * i], w[2 * i + 1], r[i]);
+}
+template <typename T>
+__device__ __forceinline__ void tmem_store_diag8(uint32_t win, int slot, T d00, T d11) {
+  uint32_t w[4];
+  to_words(d00, w[0], w[1]);
+  to_words(d11, w[2], w[3]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(win + (uint32_t)(TmLayout<T>::DIAG + 4 * slot)),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+      : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void tmem_load_diag8(uint32_t win, int slot, T& d00, T& d11) {
+  uint32_t w[4];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+      : "r"(win + (uint32_t)(TmLayout<T>::DIAG + 4 * slot))
+      : "memory");
+  from_words(w[0], w[1], d00);
+  from_words(w[2], w[3], d11);
+}
+__device__ __forceinline__ void tmem_store_rec(uint32_t win, int slot, const double (&r)[NV]) {
+  tmem_store_rec8(win, slot, r);
+}
+__device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, double (&r)[NV]) { tmem_load_rec8(win, slot, r); }
+__device__ __forceinline__ void tmem_store_rec(uint32_t win, int slot, const dfloat (&r)[NV]) {
+  tmem_store_rec8(win, slot, r);
+}
+__device__ __forceinline__ void tmem_load_rec(uint32_t win, int slot, dfloat (&r)[NV]) { tmem_load_rec8(win, slot, r); }
+__device__ __forceinline__ void tmem_store_diag(uint32_t win, int slot, double d00, double d11) {
+  tmem_store_diag8(win, slot, d00, d11);
+}
+__device__ __forceinline__ void tmem_load_diag(uint32_t win, int slot, double& d00, double& d11) {
+  tmem_load_diag8(win, slot, d00, d11);
+}
+__device__ __forceinline__ void tmem_store_diag(uint32_t win, int slot, dfloat d00, dfloat d11) {
+  tmem_store_diag8(win, slot, d00, d11);
+}
+__device__ __forceinline__ void tmem_load_diag(uint32_t win, int slot, dfloat& d00, dfloat& d11) {
+  tmem_load_diag8(win, slot, d00, d11);
+}
+// two columns per thread keep the shared-memory ring (no TMEM queue)
+__device__ __forceinline__ void tmem_store_diag(uint32_t, int, f32x2, f32x2) {}
+__device__ __forceinline__ void tmem_load_diag(uint32_t, int, f32x2&, f32x2&) {}
 __device__ __forceinline__ void tmem_load_rec(uint32_t, int, f32x2 (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const f32x2 (&)[NV]) {}
 
 // Allocate / release the CTA's TMEM columns (warp 0), publishing the base
 // address through shared memory.  The CTAs that shared memory lets share an
-// SM never ask for more than the 512 columns available (32 x 8: 3 x 128;
-// 32 x 16: 256), so the allocation never waits.
+// SM never ask for more than the 512 columns available (binary32 32 x 8:
+// 3 x 128; 32 x 16: 256; binary64 and double-float 32 x 8: 256, one CTA),
+// so the allocation never waits.
 template <int NCOL>
 __device__ __forceinline__ uint32_t tmem_acquire(uint32_t* smem_slot) {
   if ((threadIdx.x >> 5) == 0) {
@@ -275,9 +377,10 @@ __device__ __forceinline__ void tmem_release(uint32_t base) {
 }
 
 // This thread's TMEM window: lane quarter of its warp, column window warp / 4.
+template <typename T>
 __device__ __forceinline__ uint32_t tmem_window(uint32_t base) {
   const uint32_t w = threadIdx.x >> 5;
-  return base + (((w & 3u) * 32u) << 16) + (w >> 2) * (uint32_t)TM_COLS_PER_WARP;
+  return base + (((w & 3u) * 32u) << 16) + (w >> 2) * (uint32_t)TmLayout<T>::COLS;
 }
 
 // Stage input value in the arithmetic type (binary64 inputs to a binary32
@@ -560,7 +663,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   const int nit = nplanes + 4;
   // the window address is warp-uniform; broadcasting lane 0's copy lets the
   // compiler keep it in a uniform register for the tcgen05 operands
-  const uint32_t twin = ZT ? __shfl_sync(0xffffffffu, tmem_window(tmem_base), 0) : 0u;
+  const uint32_t twin = ZT ? __shfl_sync(0xffffffffu, tmem_window<T>(tmem_base), 0) : 0u;
   T d22 = T(0);
   T g00c = T(0), g11c = T(0);  // D1_x u0, D1_y u1 at the centre point
 
@@ -950,7 +1053,7 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     fused_stage_kernel(const StageArgs a, const Coef<T> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, TY, ZT>& sm = *reinterpret_cast<FusedSmem<T, TY, ZT>*>(smem_raw);
-  constexpr int NCOL = tmem_columns<TY>();  // TX*TY/32 = TY warps
+  constexpr int NCOL = tmem_columns<TY, T>();  // TX*TY/32 = TY warps
   uint32_t tbase = 0;
   if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
   double ke = 0.0, ens = 0.0;

@@ -275,8 +275,8 @@ def test_error_paths_fault_nothing(S):
              (16, 40, 1, 1), (8, 4, 1, 1), (16, 4, 1, 1), (8, 4, 0, 2), (8, 13, 0, 2), (8, 40, 0, 2)]),
         (2, [(8, 4, 0, 1), (16, 7, 0, 1), (8, 13, 1, 1), (16, 40, 1, 1), (16, 5, 1, 1), (8, 5, 0, 2),
              (8, 40, 0, 2)]),
-        (0, [(8, 4, 0, 1), (8, 9, 0, 1), (8, 40, 0, 1)]),
-        (3, [(8, 4, 0, 1), (8, 40, 0, 1)]),
+        (0, [(8, 4, 0, 1), (8, 9, 0, 1), (8, 40, 0, 1), (8, 4, 1, 1), (8, 13, 1, 1)]),
+        (3, [(8, 4, 0, 1), (8, 40, 0, 1), (8, 5, 1, 1), (8, 40, 1, 1)]),
     ],
 )
 @pytest.mark.parametrize("n", [(64, 48, 40), (96, 20, 12), (40, 9, 7)])
@@ -348,8 +348,9 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     with pytest.raises(S.SbliError):
         g.set_config(8, 8, 2)
     d = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
+    d.set_config(8, 8, 1)  # binary64 records in the TMEM queue
     with pytest.raises(S.SbliError):
-        d.set_config(8, 8, 1)  # the TMEM queue holds binary32 records only
+        d.set_config(16, 8, 1)  # binary64 tiles are 32 x 8
     with pytest.raises(S.SbliError):
         d.set_config(8, 8, 0, 2)  # two columns per thread: binary32 only
     with pytest.raises(S.SbliError):
