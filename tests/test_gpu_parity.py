@@ -350,7 +350,9 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     d = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
     d.set_config(8, 8, 1)  # binary64 records in the TMEM queue
     with pytest.raises(S.SbliError):
-        d.set_config(16, 8, 1)  # binary64 tiles are 32 x 8
+        d.set_config(4, 8, 1)  # binary64 tiles are 32 x 8
+    with pytest.raises(S.SbliError):
+        d.set_config(16, 8, 1)
     with pytest.raises(S.SbliError):
         d.set_config(8, 8, 0, 2)  # two columns per thread: binary32 only
     with pytest.raises(S.SbliError):
