@@ -150,3 +150,22 @@ def test_missing_library_fails_loudly(sbli, monkeypatch):
         sbli.lib()
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         sbli.sbli_workspace_bytes(16, 16, 16, sbli.SBLI_FP64, sbli.SBLI_FUSED)
+
+
+def test_product_package_never_loads_the_oracle():
+    """The oracle is test infrastructure: importing every module of the
+    product package loads nothing from oracle/, and no CUDA source includes
+    an oracle header."""
+    import subprocess
+    import sys
+
+    code = ("import sys; import paper_1709_09713_gb300, paper_1709_09713_gb300.sbli, paper_1709_09713_gb300.build, "
+            "paper_1709_09713_gb300.history, paper_1709_09713_gb300.workloads; "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; print(bad); "
+            "sys.exit(1 if bad else 0)")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    csrc = os.path.join(ROOT, "paper_1709_09713_gb300", "csrc")
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "sbli_oracle" not in text and "orc_" not in text, f
