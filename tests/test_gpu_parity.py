@@ -441,3 +441,37 @@ def test_init_then_get_state_every_precision(S, orc, precision):
     g.init_tgv(0.97)
     got = g.get_state().cpu().numpy()
     assert max(rel_fields(got, orc.init_tgv(orc.params(n), 0.97))) <= 1e-14
+
+
+# (Re, Mach, Pr, gamma, L): the inviscid limit (Re = inf removes the viscous
+# and heat-flux terms), a monatomic gas, unit Prandtl number, a half-size and
+# a larger domain, on a grid that is not a cube
+PHYSICS = [
+    (math.inf, 0.1, 0.71, 1.4, 1.0),
+    (400.0, 0.3, 1.0, 5.0 / 3.0, 0.5),
+    (2500.0, 0.2, 0.71, 1.4, 1.7),
+]
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-12), (1, 1e-5), (2, 1e-5)])
+@pytest.mark.parametrize("phys", PHYSICS)
+def test_physical_parameters_match_oracle(S, orc, phys, prec, tol):
+    """Every precision, on random states, with the physical parameters the
+    Taylor-Green workloads do not vary: residual (binary64 bar 1e-12,
+    binary32 residual bar 1e-4) and three steps against the oracle."""
+    Re, Mach, Pr, gamma, L = phys
+    n = (24, 20, 16)
+    e0 = 1.0 / (gamma * (gamma - 1.0) * Mach**2) + 0.5
+    q = workloads.smooth_state(n, 90 + int(gamma * 10), offsets=(1.0, 0.0, 0.0, 0.0, e0),
+                               amplitudes=(0.05, 0.4, 0.4, 0.4, 0.4))
+    p = orc.params(n, Re=Re, Mach=Mach, Pr=Pr, gamma=gamma, L=L)
+    dt = 2e-4 * L
+    g = S.Grid(n, prec, S.SBLI_FUSED, Re=Re, Mach=Mach, Pr=Pr, gamma=gamma, L=L)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    assert max(rel_fields(r, orc.rhs(p, q))) <= (tol if tol < 1e-6 else 1e-4), phys
+    g.step_n(3, dt)
+    got = g.get_state().cpu().numpy()
+    errs = rel_fields(got, orc.step(p, q, dt, 3))
+    assert max(errs) <= tol, (phys, errs)
+    g.close()
