@@ -475,3 +475,29 @@ def test_physical_parameters_match_oracle(S, orc, phys, prec, tol):
     errs = rel_fields(got, orc.step(p, q, dt, 3))
     assert max(errs) <= tol, (phys, errs)
     g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-12), (1, 1e-4), (2, 1e-4)])
+def test_uniform_flow_is_steady(S, prec, tol):
+    """A uniform state moving with a uniform velocity is steady: its residual
+    is only rounding (the streamed stencil sums of equal values, and the
+    second-derivative centre coefficient against its neighbours; binary64:
+    ~1e-15, binary32: below 1e-4 of the field scales), and the state stays
+    put."""
+    n = (37, 20, 19)
+    rho, u, p = 1.3, (0.2, -0.1, 0.05), 1.0 / (GAMMA * MACH**2) * 1.1
+    E = p / (GAMMA - 1.0) + 0.5 * rho * sum(v * v for v in u)
+    q = np.empty((5, n[2], n[1], n[0]))
+    q[0] = rho
+    for i in range(3):
+        q[1 + i] = rho * u[i]
+    q[4] = E
+    g = S.Grid(n, prec, S.SBLI_FUSED)
+    g.set_state(to_dev(q))
+    r = g.rhs().cpu().numpy()
+    scale = np.array([1.0, 1.0, 1.0, 1.0, E])
+    assert max(float(np.max(np.abs(r[f]))) / scale[f] for f in range(5)) <= tol
+    g.step_n(5, 1e-3)
+    got = g.get_state().cpu().numpy()
+    assert max(rel_fields(got, q)) <= (1e-14 if prec in (0, 3) else 1e-6)
+    g.close()
