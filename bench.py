@@ -591,6 +591,9 @@ def run_ours(args):
                         ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws, nvml=nvml),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
+                                    fp64_as=S.SBLI_DF64),
+                        # below saturation: latency close to each request's own service time
+                        serving_leg(S, args.serve_requests, 5.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
                                     fp64_as=S.SBLI_DF64)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_n, args.cpu_sample_steps, dt)
