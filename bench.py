@@ -260,8 +260,17 @@ def cpu_baseline(n: int, steps: int, dt: float):
     t0 = time.perf_counter()
     oracle.step(p, q, dt, steps)
     el = time.perf_counter() - t0
-    return {"value": n**3 * 3 * steps / el, "unit": "pt-stage/s", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"TGV {n}^3 FP64, {steps} time steps ({3 * steps} stages) in {el:.2f} s"}
+    cores = oracle.get_threads()
+    # the same oracle on one core, one time step
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.step(p, q, dt, 1)
+    el1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    return {"value": n**3 * 3 * steps / el, "unit": "pt-stage/s", "cores": cores, "kind": "oracle",
+            "sample": f"TGV {n}^3 FP64, {steps} time steps ({3 * steps} stages) in {el:.2f} s",
+            "single_thread": {"value": n**3 * 3 / el1, "unit": "pt-stage/s", "cores": 1,
+                              "sample": f"TGV {n}^3 FP64, 1 time step in {el1:.2f} s"}}
 
 
 def time_steps(S, g, stream, steps, dt, ws):
