@@ -501,3 +501,34 @@ def test_uniform_flow_is_steady(S, prec, tol):
     got = g.get_state().cpu().numpy()
     assert max(rel_fields(got, q)) <= (1e-14 if prec in (0, 3) else 1e-6)
     g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_host_buffers_equal_device_buffers(S, prec):
+    """The state read and written through host memory (pageable and pinned,
+    the path the end-to-end measurement takes) is bit for bit the state
+    through device memory, for single grids and batch members."""
+    n = (24, 20, 12)
+    q = random_state(n, 606)
+    g = S.Grid(n, prec, S.SBLI_FUSED)
+    g.set_state(torch.from_numpy(q))  # pageable host
+    a = g.get_state()
+    g.set_state(to_dev(q))
+    assert torch.equal(g.get_state(), a)
+    g.step_n(2, 1e-3)
+    dev = g.get_state()
+    pinned = torch.empty(g.shape, dtype=torch.float64).pin_memory()
+    g.get_state(pinned)
+    pageable = torch.empty(g.shape, dtype=torch.float64)
+    g.get_state(pageable)
+    assert torch.equal(pinned, dev.cpu()) and torch.equal(pageable, dev.cpu())
+    g.close()
+    if prec != 2:  # batches: binary64, binary32 and double-float arithmetic
+        b = S.Batch([n, (16, 16, 16)], prec)
+        b.init_tgv([1.0, 1.0])
+        b.set_state(0, torch.from_numpy(q))
+        b.step_n(2, 1e-3)
+        out = torch.empty(b.shape(0), dtype=torch.float64)
+        b.get_state(0, out)
+        assert torch.equal(out, b.get_state(0).cpu())
+        b.close()
