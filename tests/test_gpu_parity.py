@@ -256,7 +256,16 @@ def test_error_paths_fault_nothing(S):
         g.step_n(1, 1e-3)
     g.rk_stage(1, 1e-3)
     g.rk_stage(2, 1e-3)
-    g.get_state()
+    before = g.get_state()
+    stages = S.sbli_stage_count(g.handle)
+    g.step_n(0, 1e-3)  # zero steps: nothing runs
+    assert torch.equal(g.get_state(), before) and S.sbli_stage_count(g.handle) == stages
+    with pytest.raises(S.SbliError):
+        g.step_n(-1, 1e-3)
+    with pytest.raises(S.SbliError):
+        g.step_n(1, float("nan"))
+    with pytest.raises(S.SbliError):
+        S.sbli_sample_state(g.handle, 0, -1, 0)  # negative count
     small = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(S.SbliError) as e:
         S.sbli_create_grid(16, 16, 16, 0, 0, S.params(), (small.data_ptr() + 255) // 256 * 256, 512, 0)
