@@ -78,17 +78,10 @@ __global__ void __launch_bounds__(256) batch_ke_finalize(const double* __restric
 template <>
 cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s) {
   const size_t smem = sizeof(FusedSmem<float, 8, true>);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, false, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, double, float, 8, true, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<float, float, float, 8, false, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    cfg = true;
-  }
+  static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0};
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, double, float, 8, false, true>, smem, d0)) return e;
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, double, float, 8, true, true>, smem, d1)) return e;
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, false, true>, smem, d2)) return e;
   if (in64) {
     if (p.ke_items) batch_stage_kernel<float, double, float, 8, true, true><<<grid, TX * 8, smem, s>>>(p);
     else batch_stage_kernel<float, double, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
@@ -101,15 +94,9 @@ cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int gr
 template <>
 cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s) {
   const size_t smem = sizeof(FusedSmem<dfloat, 8>);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<dfloat, double, double, 8, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<dfloat, double, double, 8, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    cfg = true;
-  }
+  static std::atomic<unsigned long long> d0{0}, d1{0};
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<dfloat, double, double, 8, false>, smem, d0)) return e;
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<dfloat, double, double, 8, true>, smem, d1)) return e;
   if (p.ke_items) batch_stage_kernel<dfloat, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
   else batch_stage_kernel<dfloat, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
   return cudaGetLastError();
@@ -118,15 +105,9 @@ cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid,
 template <>
 cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s) {
   const size_t smem = sizeof(FusedSmem<double, 8>);
-  static bool cfg = false;
-  if (!cfg) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<double, double, double, 8, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_kernel<double, double, double, 8, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    cfg = true;
-  }
+  static std::atomic<unsigned long long> d0{0}, d1{0};
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<double, double, double, 8, false>, smem, d0)) return e;
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<double, double, double, 8, true>, smem, d1)) return e;
   if (p.ke_items) batch_stage_kernel<double, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
   else batch_stage_kernel<double, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
   return cudaGetLastError();

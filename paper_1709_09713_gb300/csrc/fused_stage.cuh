@@ -48,6 +48,7 @@
 // only through the reference enthalpy term -H0 div u).
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -1072,17 +1073,28 @@ inline dim3 fused_grid(const Geom& g, int zc) {
   return dim3((g.n0 + W - 1) / W, (g.n1 + TY - 1) / TY, (g.n2 + zc - 1) / zc);
 }
 
+// The dynamic shared-memory limit is a per-device attribute of a kernel: set
+// it on the current device the first time a kernel launches there (bit d of
+// `done`).  Concurrent first launches may both set it, which is harmless.
+template <typename K>
+cudaError_t ensure_smem_limit(K kernel, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool WITH_KE, bool DF = false,
           bool ZT = false>
 cudaError_t launch_fused_t(const StageArgs& a, const Coef<T>& c, cudaStream_t s) {
   auto k = fused_stage_kernel<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF, ZT>;
   const size_t smem = sizeof(FusedSmem<T, TY, ZT>);
-  static bool configured = false;  // one attribute call per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> done{0};  // devices this instantiation is configured on
+  if (cudaError_t e = ensure_smem_limit(k, smem, done)) return e;
   k<<<fused_grid<TY, tile_width<T>()>(a.g, a.zc), TX * TY, smem, s>>>(a, c);
   return cudaGetLastError();
 }
