@@ -135,3 +135,21 @@ def test_full_ensemble_against_single_grids_and_oracle(S, orc):
             assert err <= 1e-5, (k, m, f, err)
     b.close()
     print(f"64-member ensemble, one step: worst sampled field error {worst:.2e}")
+
+
+@pytest.mark.parametrize("precision", [0, 1, 3])
+def test_batch_of_extreme_shapes_equals_single_grids(S, precision):
+    """Members long in one axis and at the 5-point minimum in the others
+    (partial tiles in x0 and x1, z chunks from 5 to 300 planes) in one
+    persistent launch: each equals its solo run bit for bit."""
+    sizes = [(5, 5, 300), (700, 5, 5), (9, 260, 5), (33, 17, 9)]
+    b = S.Batch(sizes, precision, Re=[400.0, 900.0, 1600.0, 100.0], Mach=[0.1, 0.2, 0.3, 0.4])
+    b.init_tgv([1.0, 0.95, 1.05, 0.9])
+    b.step_n(3, 1e-3)
+    for m, n in enumerate(sizes):
+        g = S.Grid(n, precision, S.SBLI_FUSED, Re=[400.0, 900.0, 1600.0, 100.0][m], Mach=[0.1, 0.2, 0.3, 0.4][m])
+        g.init_tgv([1.0, 0.95, 1.05, 0.9][m])
+        g.step_n(3, 1e-3)
+        assert torch.equal(b.get_state(m), g.get_state()), (m, n)
+        g.close()
+    b.close()

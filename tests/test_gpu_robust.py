@@ -106,7 +106,7 @@ def test_config_changes_between_steps(S, precision):
     assert torch.equal(g.get_state(), ref.get_state())
 
 
-ODD = [(7, 13, 11), (33, 17, 9), (100, 5, 6), (65, 31, 19)]
+ODD = [(7, 13, 11), (33, 17, 9), (100, 5, 6), (65, 31, 19), (5, 5, 300), (700, 5, 5), (9, 260, 5)]
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (3, 1e-12), (1, 1e-5), (2, 1e-5)])
