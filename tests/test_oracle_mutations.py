@@ -56,6 +56,8 @@ MUTANTS = {
     "dissipation_transposed": [("L->d_u[i][j] + L->d_u[j][i] -", "L->d_u[i][j] + L->d_u[i][j] -")],
     "conductivity_without_prandtl": [("p->Mach * p->Mach * p->Pr)", "p->Mach * p->Mach)")],
     "heat_flux_sign": [("+ kappa * heat;", "- kappa * heat;")],
+    "dissipation_dilatation_coefficient": [("2.0 / 3.0 * div_u : 0.0", "1.0 / 3.0 * div_u : 0.0")],
+    "viscous_work_sign": [("- pwork + vwork +", "- pwork - vwork +")],
     # Eq. 8 / Fig. 1 coefficients
     "rk_stage_a3": [("{2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0}", "{2.0 / 3.0, 5.0 / 12.0, 3.0 / 4.0}")],
     "rk_accumulator_b2": [("{1.0 / 4.0, 3.0 / 20.0, 3.0 / 5.0}", "{1.0 / 4.0, 3.0 / 10.0, 3.0 / 5.0}")],
@@ -64,6 +66,11 @@ MUTANTS = {
     "tgv_density_mach": [("const double rho = g * M * M * pr;", "const double rho = g * M * pr;")],
     "tgv_internal_energy": [("pr / (g - 1.0) + 0.5 * rho", "pr / g + 0.5 * rho")],
     "ke_half": [("csum_add(&k_sum, 0.5 * rho *", "csum_add(&k_sum, rho *")],
+    "ke_normalisation": [("*ke = (k_sum.s + k_sum.c) / (double)P;", "*ke = (k_sum.s + k_sum.c) / (double)(P - 1);")],
+    "enstrophy_normalisation": [("*ens = (e_sum.s + e_sum.c) / (double)P;",
+                                 "*ens = (e_sum.s + e_sum.c) / (double)(P + 1);")],
+    "window_axes_swapped": [("wrap(origin[0] + a, p->n[0]), wrap(origin[1] + b, p->n[1])",
+                             "wrap(origin[1] + a, p->n[0]), wrap(origin[0] + b, p->n[1])")],
     "vorticity_sign": [("du[(size_t)(3 * 2 + 1) * P + n] - du[(size_t)(3 * 1 + 2) * P + n]",
                         "du[(size_t)(3 * 2 + 1) * P + n] + du[(size_t)(3 * 1 + 2) * P + n]")],
 }
