@@ -23,15 +23,17 @@
 //     each axis streams its four neighbour records through the accumulators
 //     one at a time (axis_terms_stream; the double-float type keeps the
 //     difference-first form, axis_terms);
-//   * ZT (binary32): each thread keeps its own column's records of the five
-//     ring planes, and their D1_x u0 / D1_y u1, in tensor memory (TMEM), so
-//     the x2 derivatives read TMEM and shared memory keeps full records only
-//     for the entering, middle and centre planes, plus u_2 of the five planes
-//     for D1_z u_2 on the halo: 64 KiB per 32 x 8 CTA, three CTAs per SM.
-//     32 x 16 tiles (one CTA per SM) keep a fourth full-record plane (the one
-//     that was the centre one plane earlier): the next entering plane then
-//     overwrites a slot nobody reads any more, so the barrier that ends each
-//     plane is not needed (two barriers per plane instead of three);
+//   * ZT (the z queue): each thread keeps its own column's records of the
+//     five ring planes, and their D1_x u0 / D1_y u1, in tensor memory (TMEM),
+//     so the x2 derivatives read TMEM and shared memory keeps full records
+//     only for the entering, middle and centre planes, plus u_2 of the five
+//     planes for D1_z u_2 on the halo: binary32 64 KiB per 32 x 8 CTA, three
+//     CTAs per SM (binary64 and double-float records take two TMEM columns
+//     per value: 127 KiB, one CTA).  32 x 16 binary32 tiles (one CTA per SM)
+//     keep a fourth full-record plane (the one that was the centre one plane
+//     earlier): the next entering plane then overwrites a slot nobody reads
+//     any more, so the barrier that ends each plane is not needed (two
+//     barriers per plane instead of three);
 //   * the arithmetic type T is double, float, dfloat (double-float, binary64
 //     storage) or f32x2 (two columns per thread in packed FP32x2 instructions);
 //   * the mixed second derivatives of the stress divergence use, for each i,
