@@ -1,7 +1,6 @@
 """Continuous-batching serving loop: requests of different sizes, step
 counts and precisions, arriving while others run, admitted by free memory;
 each result is the same (bitwise) as the request run alone."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
