@@ -309,17 +309,19 @@ def energy_per_pt_stage(g, stream, points, stage_ms, dt, nvml, seconds=1.0):
             "source": "nvmlDeviceGetTotalEnergyConsumption delta over further steps after the timed ones"}
 
 
-def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None):
+def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None, precision=None):
     """64 Taylor-Green members, N uniform over {32,48,64,96,128}, Re ~ U[100,1600],
     M ~ U[0.1,0.4], amplitude ~ U(0.9,1.1); binary32 stages with a binary64
-    accumulator; one persistent launch per stage, graph-captured steps."""
+    accumulator (or, precision SBLI_FP32_DF, a double-float one); one
+    persistent launch per stage, graph-captured steps."""
     import torch
 
     from paper_1709_09713_gb300 import workloads
 
     members = workloads.ensemble(count, seed=seed)
+    prec = S.SBLI_FP32 if precision is None else precision
     stream = torch.cuda.Stream()
-    b = S.Batch([m.n for m in members], S.SBLI_FP32, Re=[m.Re for m in members], Mach=[m.Mach for m in members],
+    b = S.Batch([m.n for m in members], prec, Re=[m.Re for m in members], Mach=[m.Mach for m in members],
                 stream=stream)
     with torch.cuda.stream(stream):
         b.init_tgv([m.amplitude for m in members])
@@ -338,8 +340,9 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None):
     b.close()
     del b
     torch.cuda.empty_cache()
+    acc = "f64 accumulator" if prec == S.SBLI_FP32 else "double-float accumulator"
     return {"workload": f"ensemble of {count} TGV grids (N in {{32,48,64,96,128}}, Re U[100,1600], M U[0.1,0.4]), "
-                        "fp32 + f64 accumulator, persistent launch per stage", "value": 3.0 * pts * steps * ws / (ms / 1e3),
+                        f"fp32 + {acc}, persistent launch per stage", "value": 3.0 * pts * steps * ws / (ms / 1e3),
             "unit": "pt-stage/s", "steps": steps, "points": pts, "work_items_per_stage": items,
             "stage_ms": ms / (3 * steps), "launches_per_stage": 1, "energy": energy}
 
@@ -598,6 +601,7 @@ def run_ours(args):
                         leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
                         algorithms_leg(S, 256, args.alg_steps, 1, dt, ws, nvml),
                         ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws, nvml=nvml),
+                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws, nvml=nvml, precision=S.SBLI_FP32_DF),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
                                     fp64_as=S.SBLI_DF64),

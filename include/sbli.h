@@ -234,10 +234,10 @@ SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_
  * Batched ensembles: up to 64 members (each its own grid size, Re, M, Pr,
  * gamma, L) advanced together.  Every Runge-Kutta stage of all members is one
  * persistent kernel launch that walks the members' work items (z chunk x
- * 32 x 8 tile); step loops are captured as CUDA graphs.  Precision
- * SBLI_FP64, SBLI_FP32 or SBLI_DF64, as for single grids (others:
- * SBLI_EINVAL).  Members' results are bitwise those of the same member run
- * alone as a single grid with tile height 8.
+ * 32 x 8 tile); step loops are captured as CUDA graphs.  Any precision of
+ * sbli_precision, as for single grids (others: SBLI_EINVAL).  Members'
+ * results are bitwise those of the same member run alone as a single grid
+ * with tile height 8.
  * n: 3*count edge lengths (n0, n1, n2 per member); params: count entries.
  * --------------------------------------------------------------------- */
 typedef struct sbli_batch sbli_batch;

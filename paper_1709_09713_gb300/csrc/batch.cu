@@ -22,8 +22,9 @@
 namespace sbli {
 
 // ZT: x2-neighbour records in a TMEM queue and the 3-slot shared ring (binary32),
-// the CTA's TMEM columns held for all of its work items.
-template <typename T, typename TIN, typename TOUT, int TY, bool WITH_KE, bool ZT = false>
+// the CTA's TMEM columns held for all of its work items.  DF: binary32 stages
+// with the double-float accumulator (SBLI_FP32_DF members).
+template <typename T, typename TIN, typename TOUT, int TY, bool WITH_KE, bool ZT = false, bool DF = false>
 __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     batch_stage_kernel(const __grid_constant__ BatchParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -47,8 +48,8 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     const int bx = tile % p.tiles_x[lo], by = tile / p.tiles_x[lo];
     const int zbeg = chunk * a.zc;
     double ke = 0.0, ens = 0.0;
-    fused_march<T, TIN, TOUT, TY, false, WITH_KE, false, ZT>(a, p.c[lo], bx, by, zbeg, zbeg + a.zc, sm, ke, ens,
-                                                               tbase);
+    fused_march<T, TIN, TOUT, TY, false, WITH_KE, DF, ZT>(a, p.c[lo], bx, by, zbeg, zbeg + a.zc, sm, ke, ens,
+                                                            tbase);
     if (WITH_KE) block_reduce_pair<TX * TY>(sm.red, ke, ens, p.ke_items + 2 * item);
   }
   if (ZT) tmem_release<NCOL>(tbase);
@@ -76,8 +77,18 @@ __global__ void __launch_bounds__(256) batch_ke_finalize(const double* __restric
 // binary32 members: TMEM z queue and 3-slot ring, 3 CTAs per SM (the grid is
 // sized for that by the caller: batch_ctas_per_sm)
 template <>
-cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s) {
+cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s, bool df) {
   const size_t smem = sizeof(FusedSmem<float, 8, true>);
+  if (df) {  // double-float accumulator: every stage input is binary32
+    static std::atomic<unsigned long long> f0{0}, f1{0};
+    if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, false, true, true>, smem, f0))
+      return e;
+    if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, true, true, true>, smem, f1))
+      return e;
+    if (p.ke_items) batch_stage_kernel<float, float, float, 8, true, true, true><<<grid, TX * 8, smem, s>>>(p);
+    else batch_stage_kernel<float, float, float, 8, false, true, true><<<grid, TX * 8, smem, s>>>(p);
+    return cudaGetLastError();
+  }
   static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0};
   if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, double, float, 8, false, true>, smem, d0)) return e;
   if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, double, float, 8, true, true>, smem, d1)) return e;
@@ -92,7 +103,7 @@ cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int gr
 }
 
 template <>
-cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s) {
+cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s, bool) {
   const size_t smem = sizeof(FusedSmem<dfloat, 8>);
   static std::atomic<unsigned long long> d0{0}, d1{0};
   if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<dfloat, double, double, 8, false>, smem, d0)) return e;
@@ -103,7 +114,7 @@ cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid,
 }
 
 template <>
-cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s) {
+cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s, bool) {
   const size_t smem = sizeof(FusedSmem<double, 8>);
   static std::atomic<unsigned long long> d0{0}, d1{0};
   if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<double, double, double, 8, false>, smem, d0)) return e;
@@ -242,6 +253,14 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
     if (k == 0) { a.q_in = S; a.acc_in = S; a.acc_out = A; a.q_out = B; }
     else if (k == 1) { a.q_in = B; a.acc_in = A; a.acc_out = A; a.q_out = S; }
     else { a.q_in = S; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
+  } else if (b->precision == SBLI_FP32_DF) {
+    // state and accumulator as double-float pairs (hi fields, then lo fields)
+    float* S = reinterpret_cast<float*>(r64(state));
+    float* A = reinterpret_cast<float*>(r64(1 - state));
+    *in64 = false;
+    if (k == 0) { a.q_in = S; a.dacc_in = S; a.dacc_out = A; a.q_out = r32(0); }
+    else if (k == 1) { a.q_in = r32(0); a.dacc_in = A; a.dacc_out = A; a.q_out = r32(1); }
+    else { a.q_in = r32(1); a.dacc_in = A; a.dacc_out = A; a.q_out = nullptr; }
   } else {
     double* S = r64(state);
     double* A = r64(1 - state);
@@ -271,7 +290,7 @@ cudaError_t enqueue_batch_stage_t(sbli_batch* b, int k, int state, double dt, do
   }
   p.item_begin[b->count] = acc;
   p.total_items = acc;
-  return launch_batch_t<T>(p, in64, b->grid_ctas, s);
+  return launch_batch_t<T>(p, in64, b->grid_ctas, s, b->precision == SBLI_FP32_DF);
 }
 
 cudaError_t enqueue_batch_stage(sbli_batch* b, int k, int state, double dt, double* ke_items, cudaStream_t s) {
@@ -329,8 +348,7 @@ extern "C" {
 int sbli_batch_workspace_bytes(int count, const int* n, int precision, size_t* bytes) {
   if (!bytes || !n) return bfail(SBLI_EINVAL, "null argument");
   if (count < 1 || count > BATCH_MAX_MEMBERS) return bfail(SBLI_EINVAL, "count %d not in 1..%d", count, BATCH_MAX_MEMBERS);
-  if (precision != SBLI_FP64 && precision != SBLI_FP32 && precision != SBLI_DF64)
-    return bfail(SBLI_EINVAL, "precision %d not available for batches (binary64, binary32, double-float)", precision);
+  if (precision < SBLI_FP64 || precision > SBLI_DF64) return bfail(SBLI_EINVAL, "unknown precision %d", precision);
   for (int i = 0; i < count; ++i) {
     const int* m = n + 3 * i;
     if (m[0] < 5 || m[1] < 5 || m[2] < 5 || (long long)m[0] * m[1] >= (1LL << 31) ||
@@ -432,6 +450,15 @@ int sbli_batch_init_tgv(sbli_batch* b, const double* amplitudes) {
   for (int m = 0; m < b->count; ++m) {
     if (!isfinite(amplitudes[m])) return bfail(SBLI_EINVAL, "amplitude %d not finite", m);
     const MemberLayout& M = b->L.m[m];
+    if (b->precision == SBLI_FP32_DF) {
+      // binary64 deviation field into the free register, then split into hi/lo
+      double* tmp = reinterpret_cast<double*>(b->reg64[1] + M.off64);
+      SBLI_BTRY(launch_init_tgv(member_geom(M), b->params[m], amplitudes[m], tmp, b->stream), "init_tgv");
+      SBLI_BTRY(launch_df_split(M.P, RefState{0.0, 0.0}, tmp, reinterpret_cast<float*>(b->reg64[0] + M.off64),
+                                b->stream),
+                "df_split");
+      continue;
+    }
     SBLI_BTRY(launch_init_tgv(member_geom(M), b->params[m], amplitudes[m],
                               reinterpret_cast<double*>(b->reg64[0] + M.off64), b->stream),
               "init_tgv");
@@ -448,7 +475,12 @@ int sbli_batch_set_state(sbli_batch* b, int member, const double* q, int q_is_ho
   SBLI_BTRY(cudaMemcpyAsync(tmp, q, 5 * M.P * sizeof(double), q_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             b->stream),
             "cudaMemcpyAsync");
-  SBLI_BTRY(launch_to_offset(member_geom(M), make_ref(b->params[member]), tmp, dst, b->stream), "to_offset");
+  if (b->precision == SBLI_FP32_DF) {
+    SBLI_BTRY(launch_df_split(M.P, make_ref(b->params[member]), tmp, reinterpret_cast<float*>(dst), b->stream),
+              "df_split");
+  } else {
+    SBLI_BTRY(launch_to_offset(member_geom(M), make_ref(b->params[member]), tmp, dst, b->stream), "to_offset");
+  }
   if (q_is_host) SBLI_BTRY(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
   return SBLI_OK;
 }
@@ -459,7 +491,12 @@ int sbli_batch_get_state(sbli_batch* b, int member, double* q, int q_is_host) {
   const MemberLayout& M = b->L.m[member];
   const double* src = reinterpret_cast<double*>(b->reg64[b->state] + M.off64);
   double* tmp = reinterpret_cast<double*>(b->reg64[(b->state + 1) % b->L.n64] + M.off64);
-  SBLI_BTRY(launch_from_offset(member_geom(M), make_ref(b->params[member]), src, tmp, b->stream), "from_offset");
+  if (b->precision == SBLI_FP32_DF) {
+    SBLI_BTRY(launch_df_join(M.P, make_ref(b->params[member]), reinterpret_cast<const float*>(src), tmp, b->stream),
+              "df_join");
+  } else {
+    SBLI_BTRY(launch_from_offset(member_geom(M), make_ref(b->params[member]), src, tmp, b->stream), "from_offset");
+  }
   SBLI_BTRY(cudaMemcpyAsync(q, tmp, 5 * M.P * sizeof(double), q_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                             b->stream),
             "cudaMemcpyAsync");
@@ -508,9 +545,15 @@ int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstrophy) {
   if (!ke || !enstrophy) return bfail(SBLI_EINVAL, "null output");
   for (int m = 0; m < b->count; ++m) {
     const MemberLayout& M = b->L.m[m];
-    SBLI_BTRY(launch_ke(member_geom(M), make_coef<double>(M.n, b->params[m]), make_ref(b->params[m]),
-                        reinterpret_cast<double*>(b->reg64[b->state] + M.off64), b->ke_scratch, b->ke_out + 2 * m,
-                        b->stream),
+    const double* q = reinterpret_cast<double*>(b->reg64[b->state] + M.off64);
+    if (b->precision == SBLI_FP32_DF) {  // join into the register free at a step boundary
+      double* tmp = reinterpret_cast<double*>(b->reg64[1 - b->state] + M.off64);
+      SBLI_BTRY(launch_df_join(M.P, RefState{0.0, 0.0}, reinterpret_cast<const float*>(q), tmp, b->stream),
+                "df_join");
+      q = tmp;
+    }
+    SBLI_BTRY(launch_ke(member_geom(M), make_coef<double>(M.n, b->params[m]), make_ref(b->params[m]), q,
+                        b->ke_scratch, b->ke_out + 2 * m, b->stream),
               "ke");
   }
   std::vector<double> h(2 * b->count);

@@ -21,14 +21,16 @@ struct BatchParams {
 };
 
 // One persistent launch of stage work for p.count members (grid = CTAs).
-// in64: the members' stage inputs are binary64 (binary32 path, stage 0).
+// in64: the members' stage inputs are binary64 (binary32 path, stage 0);
+// df: binary32 stages with the double-float accumulator (dacc pointers).
 template <typename T>
-cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStream_t s);
+cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStream_t s, bool df = false);
 
-// Resident CTAs per SM of the multi-member launch: binary32 members run the
-// TMEM-queue kernel (64 KiB shared, 80 registers: 3 per SM), binary64 and
-// double-float members the 194.5 KiB shared-ring kernel (1 per SM).
-inline int batch_ctas_per_sm(int precision) { return precision == SBLI_FP32 ? 3 : 1; }
+// Resident CTAs per SM of the multi-member launch: binary32 members (either
+// accumulator) run the TMEM-queue kernel (64 KiB shared, 80 registers: 3 per
+// SM), binary64 and double-float-arithmetic members the 194.5 KiB
+// shared-ring kernel (1 per SM).
+inline int batch_ctas_per_sm(int precision) { return precision == SBLI_FP32 || precision == SBLI_FP32_DF ? 3 : 1; }
 
 // Work items (z chunk x 32 x 8 tile) of one member and its planes per item.
 inline int batch_zc(int n2) { return n2 < 32 ? n2 : 32; }

@@ -173,11 +173,11 @@ def test_product_package_never_loads_the_oracle():
 
 def test_batch_limits(sbli):
     """Batches take 1..64 members (the member table is a kernel parameter),
-    binary64, binary32 or double-float arithmetic, and the single-grid size
-    rules per member."""
+    every precision, and the single-grid size rules per member."""
     ok = sbli.sbli_batch_workspace_bytes([(16, 16, 16)] * 64, sbli.SBLI_FP32)
     assert ok >= 64 * 5 * 16**3 * 4
-    for sizes, prec in (([(16, 16, 16)] * 65, sbli.SBLI_FP32), ([(16, 16, 16)], sbli.SBLI_FP32_DF),
+    assert sbli.sbli_batch_workspace_bytes([(16, 16, 16)] * 64, sbli.SBLI_FP32_DF) == ok
+    for sizes, prec in (([(16, 16, 16)] * 65, sbli.SBLI_FP32), ([(16, 16, 16)], 7),
                         ([(16, 16, 16), (4, 16, 16)], sbli.SBLI_FP64), ([(2048, 2048, 1024)], sbli.SBLI_FP64)):
         with pytest.raises(sbli.SbliError) as e:
             sbli.sbli_batch_workspace_bytes(sizes, prec)

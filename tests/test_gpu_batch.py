@@ -30,7 +30,7 @@ MACH = [0.1, 0.25, 0.4, 0.15, 0.3]
 AMP = [1.0, 0.95, 1.08, 0.9, 1.02]
 
 
-@pytest.mark.parametrize("precision", [0, 1, 3])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_batch_members_equal_single_grids_bitwise(S, precision):
     dt, steps = 1e-3, 7  # one captured 6-step graph plus one direct step
     b = S.Batch(SIZES, precision, Re=RE, Mach=MACH)
@@ -61,10 +61,11 @@ def test_batch_matches_oracle_fp64(S, orc, precision):
             assert np.max(np.abs(got[f] - want[f])) / den <= 1e-12, (m, f)
 
 
-def test_batch_history_and_set_state(S):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_history_and_set_state(S, prec):
     dt, steps = 1e-3, 3
     sizes = SIZES[:4]
-    b = S.Batch(sizes, 1, Re=RE[:4], Mach=MACH[:4])
+    b = S.Batch(sizes, prec, Re=RE[:4], Mach=MACH[:4])
     rng = np.random.default_rng(5)
     for m, n in enumerate(sizes):
         e0 = 1.0 / (1.4 * 0.4 * MACH[m] ** 2) + 0.5
@@ -73,7 +74,7 @@ def test_batch_history_and_set_state(S):
     hist = b.step_n_history(steps, dt).cpu().numpy()
     ke, ens = b.kinetic_energy()
     for m, n in enumerate(sizes):
-        g = S.Grid(n, 1, S.SBLI_FUSED, Re=RE[m], Mach=MACH[m])
+        g = S.Grid(n, prec, S.SBLI_FUSED, Re=RE[m], Mach=MACH[m])
         e0 = 1.0 / (1.4 * 0.4 * MACH[m] ** 2) + 0.5
         q = workloads.smooth_state(n, 40 + m, offsets=(1.0, 0, 0, 0, e0), amplitudes=(0.05, 0.3, 0.3, 0.3, 0.3))
         g.set_state(torch.from_numpy(q).cuda())
@@ -137,7 +138,7 @@ def test_full_ensemble_against_single_grids_and_oracle(S, orc):
     print(f"64-member ensemble, one step: worst sampled field error {worst:.2e}")
 
 
-@pytest.mark.parametrize("precision", [0, 1, 3])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_batch_of_extreme_shapes_equals_single_grids(S, precision):
     """Members long in one axis and at the 5-point minimum in the others
     (partial tiles in x0 and x1, z chunks from 5 to 300 planes) in one

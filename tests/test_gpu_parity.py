@@ -532,12 +532,11 @@ def test_host_buffers_equal_device_buffers(S, prec):
     g.get_state(pageable)
     assert torch.equal(pinned, dev.cpu()) and torch.equal(pageable, dev.cpu())
     g.close()
-    if prec != 2:  # batches: binary64, binary32 and double-float arithmetic
-        b = S.Batch([n, (16, 16, 16)], prec)
-        b.init_tgv([1.0, 1.0])
-        b.set_state(0, torch.from_numpy(q))
-        b.step_n(2, 1e-3)
-        out = torch.empty(b.shape(0), dtype=torch.float64)
-        b.get_state(0, out)
-        assert torch.equal(out, b.get_state(0).cpu())
-        b.close()
+    b = S.Batch([n, (16, 16, 16)], prec)  # batch members
+    b.init_tgv([1.0, 1.0])
+    b.set_state(0, torch.from_numpy(q))
+    b.step_n(2, 1e-3)
+    out = torch.empty(b.shape(0), dtype=torch.float64)
+    b.get_state(0, out)
+    assert torch.equal(out, b.get_state(0).cpu())
+    b.close()
