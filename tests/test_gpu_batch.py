@@ -96,7 +96,8 @@ def test_batch_ensemble_draws_build(S):
         S.sbli_batch_workspace_bytes([(4, 8, 8)], 1)
 
 
-def test_full_ensemble_against_single_grids_and_oracle(S, orc):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_ensemble_against_single_grids_and_oracle(S, orc, prec):
     """The benchmarked ensemble itself: 64 Taylor-Green members (N uniform
     over {32, 48, 64, 96, 128}, Re ~ U[100, 1600], M ~ U[0.1, 0.4], amplitude
     ~ U(0.9, 1.1), seed 1709), binary32 stages with a binary64 accumulator,
@@ -107,14 +108,14 @@ def test_full_ensemble_against_single_grids_and_oracle(S, orc):
     the binary32 bar."""
     dt = 1e-3
     members = workloads.ensemble(64, seed=1709)
-    b = S.Batch([m.n for m in members], S.SBLI_FP32, Re=[m.Re for m in members], Mach=[m.Mach for m in members])
+    b = S.Batch([m.n for m in members], prec, Re=[m.Re for m in members], Mach=[m.Mach for m in members])
     b.init_tgv([m.amplitude for m in members])
     b.step_n(1, dt)
     rng = np.random.default_rng(64)
     worst = 0.0
     for k, m in enumerate(members):
         got = b.get_state(k)
-        g = S.Grid(m.n, S.SBLI_FP32, S.SBLI_FUSED, Re=m.Re, Mach=m.Mach)
+        g = S.Grid(m.n, prec, S.SBLI_FUSED, Re=m.Re, Mach=m.Mach)
         g.init_tgv(m.amplitude)
         g.step_n(1, dt)
         assert torch.equal(got, g.get_state()), k
@@ -135,7 +136,7 @@ def test_full_ensemble_against_single_grids_and_oracle(S, orc):
             worst = max(worst, err)
             assert err <= 1e-5, (k, m, f, err)
     b.close()
-    print(f"64-member ensemble, one step: worst sampled field error {worst:.2e}")
+    print(f"64-member ensemble, precision {prec}, one step: worst sampled field error {worst:.2e}")
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2, 3])
