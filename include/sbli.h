@@ -269,9 +269,10 @@ SBLI_API int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstro
  * caller's device arena are free (first fit; with backfill != 0 a later
  * request that fits may pass one that does not).  Admitted requests keep
  * their state resident; each sbli_server_tick advances every active request
- * by one time step (binary64 and binary32 requests as two persistent
- * multi-member launches per stage on the two given streams, which overlap on
- * the device), then retires the finished ones: binary64 kinetic energy and
+ * by one time step (the requests of each precision as one persistent
+ * multi-member launch per stage; binary64-register precisions on the first
+ * stream, binary32 ones on the second, which overlap on the device), then
+ * retires the finished ones: binary64 kinetic energy and
  * enstrophy of the final state, optional copy of the state to `result`, and
  * release of the block.  A request's result equals the same problem run
  * alone as a single grid with tile height 8, bitwise.
@@ -280,7 +281,7 @@ typedef struct sbli_server sbli_server;
 
 typedef struct {
   int n0, n1, n2;      /* grid */
-  int precision;       /* SBLI_FP64, SBLI_FP32 or SBLI_DF64 */
+  int precision;       /* any sbli_precision */
   int steps;           /* time steps to run (>= 0) */
   double dt;           /* time step (> 0) */
   sbli_params params;  /* Re, M, Pr, gamma, L */

@@ -5,9 +5,10 @@
 // arena are free (first-fit allocation with coalescing of freed blocks).  An
 // admitted request's state stays resident in its block for its whole life.
 // Every tick advances all active requests by one time step: for each stage,
-// the binary64 requests and the binary32 requests are each one persistent
-// multi-member launch (batch_kernel.cuh) on their own stream, so the two
-// groups' work overlaps on the device.  Finished requests are retired at the
+// the requests of each precision form one persistent multi-member launch
+// (batch_kernel.cuh); the binary64-register groups (binary64, double-float
+// arithmetic) run on one stream and the binary32 groups (either accumulator)
+// on another, so their work overlaps on the device.  Finished requests are retired at the
 // end of the tick (binary64 kinetic energy and enstrophy, optional copy of the
 // final state to a caller buffer) and their memory is released, which lets
 // waiting requests in on the next tick.
@@ -165,6 +166,14 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
     if (k == 0) { a.q_in = S; a.acc_in = S; a.acc_out = A; a.q_out = B; }
     else if (k == 1) { a.q_in = B; a.acc_in = A; a.acc_out = A; a.q_out = S; }
     else { a.q_in = S; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
+  } else if (q.r.precision == SBLI_FP32_DF) {
+    // state and accumulator as double-float pairs (hi fields, then lo fields)
+    float* S = reinterpret_cast<float*>(r64(s, q, st));
+    float* A = reinterpret_cast<float*>(r64(s, q, 1 - st));
+    *in64 = false;
+    if (k == 0) { a.q_in = S; a.dacc_in = S; a.dacc_out = A; a.q_out = r32(s, q, 0); }
+    else if (k == 1) { a.q_in = r32(s, q, 0); a.dacc_in = A; a.dacc_out = A; a.q_out = r32(s, q, 1); }
+    else { a.q_in = r32(s, q, 1); a.dacc_in = A; a.dacc_out = A; a.q_out = nullptr; }
   } else {
     double* S = r64(s, q, st);
     double* A = r64(s, q, 1 - st);
@@ -201,7 +210,7 @@ cudaError_t launch_group(sbli_server* s, int k, int precision, cudaStream_t st, 
     }
     p.item_begin[cnt] = acc;
     p.total_items = acc;
-    cudaError_t e = launch_batch_t<T>(p, in64, grid, st);
+    cudaError_t e = launch_batch_t<T>(p, in64, grid, st, precision == SBLI_FP32_DF);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -212,8 +221,7 @@ int valid_request(const sbli_request* r) {
   if (r->n0 < 5 || r->n1 < 5 || r->n2 < 5 || (long long)r->n0 * r->n1 >= (1LL << 31) ||
       (long long)r->n0 * r->n1 * r->n2 >= (1LL << 32))
     return sfail(SBLI_EINVAL, "request grid %d x %d x %d invalid", r->n0, r->n1, r->n2);
-  if (r->precision != SBLI_FP64 && r->precision != SBLI_FP32 && r->precision != SBLI_DF64)
-    return sfail(SBLI_EINVAL, "precision %d not available for requests (binary64, binary32, double-float)", r->precision);
+  if (r->precision < SBLI_FP64 || r->precision > SBLI_DF64) return sfail(SBLI_EINVAL, "unknown precision %d", r->precision);
   if (r->steps < 0) return sfail(SBLI_EINVAL, "steps < 0");
   if (!(r->dt > 0) || !isfinite(r->dt)) return sfail(SBLI_EINVAL, "dt must be finite and > 0");
   const sbli_params& p = r->params;
@@ -229,13 +237,24 @@ int retire(sbli_server* s, Req& q) {
   const Geom g{q.r.n0, q.r.n1, q.r.n2, q.P};
   const int n[3] = {q.r.n0, q.r.n1, q.r.n2};
   const double* state = r64(s, q, q.state);
+  if (q.r.precision == SBLI_FP32_DF) {
+    // join the double-float state (deviation form) into the other register
+    double* joined = r64(s, q, 1 - q.state);
+    SBLI_STRY(launch_df_join(q.P, RefState{0.0, 0.0}, reinterpret_cast<const float*>(state), joined, st), "df_join");
+    state = joined;
+  }
   SBLI_STRY(launch_ke(g, make_coef<double>(n, q.r.params), make_ref(q.r.params), state, s->ke_scratch, s->ke_dev, st),
             "ke");
   double h[2];
   SBLI_STRY(cudaMemcpyAsync(h, s->ke_dev, sizeof h, cudaMemcpyDeviceToHost, st), "D2H");
   if (q.r.result) {
     double* tmp = r64(s, q, (q.state + 1) % 2);  // a register the finished state does not occupy
-    SBLI_STRY(launch_from_offset(g, make_ref(q.r.params), state, tmp, st), "from_offset");
+    if (q.r.precision == SBLI_FP32_DF) {
+      SBLI_STRY(launch_df_join(q.P, make_ref(q.r.params), reinterpret_cast<const float*>(r64(s, q, q.state)), tmp, st),
+                "df_join");
+    } else {
+      SBLI_STRY(launch_from_offset(g, make_ref(q.r.params), state, tmp, st), "from_offset");
+    }
     SBLI_STRY(cudaMemcpyAsync(q.r.result, tmp, 5 * (size_t)q.P * sizeof(double),
                               q.r.result_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st),
               "copy result");
@@ -335,17 +354,24 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     q.state = 0;
     q.remaining = q.r.steps;
     cudaStream_t st = req_f64_registers(q.r.precision) ? s->s64 : s->s32;
-    SBLI_STRY(launch_init_tgv(Geom{q.r.n0, q.r.n1, q.r.n2, q.P}, q.r.params, q.r.amplitude, r64(s, q, 0), st),
-              "init_tgv");
+    const Geom qg{q.r.n0, q.r.n1, q.r.n2, q.P};
+    if (q.r.precision == SBLI_FP32_DF) {  // binary64 deviation field, then split into hi/lo
+      SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 1), st), "init_tgv");
+      SBLI_STRY(launch_df_split(q.P, RefState{0.0, 0.0}, r64(s, q, 1), reinterpret_cast<float*>(r64(s, q, 0)), st),
+                "df_split");
+    } else {
+      SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 0), st), "init_tgv");
+    }
     s->active.push_back(q);
   }
   // one time step for every active request with steps left
-  bool any64 = false, any32 = false, anydw = false;
+  bool any64 = false, any32 = false, anydw = false, anydf = false;
   for (const Req& q : s->active) {
     if (q.remaining > 0)
-      (q.r.precision == SBLI_FP64 ? any64 : q.r.precision == SBLI_DF64 ? anydw : any32) = true;
+      (q.r.precision == SBLI_FP64 ? any64 : q.r.precision == SBLI_DF64 ? anydw
+                                           : q.r.precision == SBLI_FP32_DF ? anydf : any32) = true;
   }
-  if (any64 || any32 || anydw) {
+  if (any64 || any32 || anydw || anydf) {
     // requests with no steps left sit out this step
     std::vector<Req> idle;
     for (auto it = s->active.begin(); it != s->active.end();) {
@@ -360,6 +386,7 @@ int sbli_server_tick(sbli_server* s, int* completed) {
       if (any64) SBLI_STRY(launch_group<double>(s, k, SBLI_FP64, s->s64, s->grid64), "fp64 stage");
       if (anydw) SBLI_STRY(launch_group<dfloat>(s, k, SBLI_DF64, s->s64, s->grid64), "double-float stage");
       if (any32) SBLI_STRY(launch_group<float>(s, k, SBLI_FP32, s->s32, s->grid32), "fp32 stage");
+      if (anydf) SBLI_STRY(launch_group<float>(s, k, SBLI_FP32_DF, s->s32, s->grid32), "fp32 double-float stage");
     }
     for (Req& q : s->active) {
       q.state = req_f64_registers(q.r.precision) ? (q.state + 1) % 3 : 1 - q.state;

@@ -31,6 +31,8 @@ REQS = [  # n, precision, steps, Re, Mach, amplitude, submit at tick
     ((16, 16, 16), 0, 0, 1600.0, 0.1, 1.0, 6),
     ((24, 20, 16), 3, 6, 1600.0, 0.1, 1.0, 1),  # double-float arithmetic
     ((32, 16, 12), 3, 3, 300.0, 0.2, 0.97, 4),
+    ((28, 20, 12), 2, 5, 900.0, 0.25, 1.02, 1),  # binary32, double-float accumulator
+    ((16, 24, 20), 2, 8, 1600.0, 0.1, 1.0, 4),
 ]
 
 
