@@ -113,3 +113,7 @@ def test_server_rejects_bad_requests(S):
     assert e.value.code == S.SBLI_EINVAL
     with pytest.raises(S.SbliError):
         srv.submit(S.request((8, 8, 8), 0, 1, dt=-1.0))
+    with pytest.raises(S.SbliError) as e:
+        srv.submit(S.request((8, 8, 8), 7, 1))  # unknown precision
+    assert e.value.code == S.SBLI_EINVAL
+    srv.close()
