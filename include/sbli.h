@@ -28,13 +28,13 @@
  *    are binary64.  Precision SBLI_FP32_DF: as SBLI_FP32, but the accumulator
  *    and the state between steps are double-float pairs (hi + lo, two
  *    binary32, about 48 significant bits) updated with error-free binary32
- *    additions, so no binary64 arithmetic runs in the stages (fused variant,
- *    single grids only).  Precision SBLI_DF64: binary64 registers, state and
+ *    additions, so no binary64 arithmetic runs in the stages (fused variant;
+ *    single grids, batches and requests).  Precision SBLI_DF64: binary64 registers, state and
  *    accumulator exactly as SBLI_FP64, but the stage arithmetic (primitives,
  *    derivatives, residual) in double-float: each value a hi + lo pair of
  *    binary32 (about 48 significant bits) evaluated on the binary32 pipe with
  *    error-free transformations; the RK update is the binary64 FMA (fused
- *    variant, single grids only).  All store the state as deviations from the uniform
+ *    variant; single grids, batches and requests).  All store the state as deviations from the uniform
  *    reference state (rho = 1, u = 0, p = 1/(gamma M^2)); the
  *    get/set calls convert to and from the plain conserved variables.
  *  - Variant SBLI_FUSED evaluates every derivative on the fly and writes the
