@@ -85,10 +85,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
-    ap.add_argument("--profile", choices=["stage", "algorithms"], default=None,
+    ap.add_argument("--profile", choices=["stage", "algorithms", "ensemble"], default=None,
                     help="untimed runs for ncu: 'stage' = --steps steps of one grid (--n, --profile-precision, "
                          "--profile-variant) stage by stage; 'algorithms' = stage 0 of every binary64 "
-                         "algorithm class at --n")
+                         "algorithm class at --n; 'ensemble' = --steps steps of the first --profile-members "
+                         "members of the seeded ensemble (--profile-precision)")
+    ap.add_argument("--profile-members", type=int, default=16)
     ap.add_argument("--profile-precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--profile-variant", default="fused", choices=sorted(VARIANTS))
     ap.add_argument("--profile-config", default=None, help="tile_y,planes_per_cta,z_queue (default: the grid's)")
@@ -115,6 +117,16 @@ def run_profile(args):
                 g.rk_stage(k, args.dt)
         torch.cuda.synchronize()
         g.close()
+    elif args.profile == "ensemble":
+        from paper_1709_09713_gb300 import workloads
+
+        members = workloads.ensemble(64, seed=1709)[: args.profile_members]
+        b = S.Batch([m.n for m in members], PRECISIONS[args.profile_precision], Re=[m.Re for m in members],
+                    Mach=[m.Mach for m in members])
+        b.init_tgv([m.amplitude for m in members])
+        b.step_n(args.steps, args.dt)
+        torch.cuda.synchronize()
+        b.close()
     else:
         for name in ("store_all", "RS", "SS", "RA", "SN", "SN2", "fused"):
             g = S.Grid(args.n, S.SBLI_FP64, VARIANTS[name])
