@@ -251,6 +251,8 @@ cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_
     a.a_dt = a_dt;
     a.b_dt = b_dt;
     a.amb_dt = (RK_A[k] - RK_B[k]) * dt;
+    a.b_dt32 = (float)a.b_dt;
+    a.amb_dt32 = (float)a.amb_dt;
     a.ke_partials = ke_partials;
     a.dacc_in = p.dacc_in;
     a.dacc_out = p.dacc_out;

@@ -825,7 +825,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             }
           } else {
 #pragma unroll
-            for (int f = 0; f < NF; ++f) accv[f][j] = accf[f] ? accf[f][oc[j]] : double(qf[f][oc[j]]);
+            for (int f = 0; f < NF; ++f) accv[f][j] = accf[f][oc[j]];
           }
         }
       }
@@ -964,7 +964,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           // each): acc' = acc + (b dt R) by an error-free two-sum of hi and
           // the increment, the error folded into lo and renormalised;
           // Q_{k+1} = hi' + (lo' + (a - b) dt R).
-          const float bdt = float(a.b_dt), ambdt = float(a.amb_dt);
+          const float bdt = a.b_dt32, ambdt = a.amb_dt32;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const float r = float(lane(R[f], j));
@@ -992,7 +992,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           // binary32 stage, binary64 accumulator: one DADD per field,
           //   acc' = acc + (b dt R),  Q_{k+1} = float(acc') + (a - b) dt R
           // (conversions by integer re-packing, fpconv.cuh)
-          const float bdt = float(a.b_dt), ambdt = float(a.amb_dt);
+          const float bdt = a.b_dt32, ambdt = a.amb_dt32;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const float r = float(lane(R[f], j));

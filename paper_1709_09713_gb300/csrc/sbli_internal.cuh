@@ -61,12 +61,13 @@ struct StageArgs {
   Geom g;
   int zc;                  // planes per CTA along x2
   const void* q_in;        // stage input (stencil reads)
-  const double* acc_in;    // accumulator in (binary64), nullptr: use q_in (stage 0)
+  const double* acc_in;    // accumulator in (binary64; on stage 0 the state itself)
   double* acc_out;         // accumulator out (binary64), may alias acc_in
   void* q_out;             // stage output, nullptr on the last stage
   double* r_out;           // RHS-only mode: R (binary64)
   double a_dt, b_dt;       // a_k dt, b_k dt
   double amb_dt;           // (a_k - b_k) dt
+  float b_dt32, amb_dt32;  // the same rounded to binary32 on the host (binary32 stage updates)
   double* ke_partials;     // per-CTA (ke, enstrophy) partial sums, or nullptr
   // double-float accumulator (precision SBLI_FP32_DF): 5 hi fields then 5 lo
   // fields of binary32, P values each

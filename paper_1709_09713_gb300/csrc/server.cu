@@ -157,6 +157,8 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
   a.a_dt = RK_A[k] * q.r.dt;
   a.b_dt = RK_B[k] * q.r.dt;
   a.amb_dt = (RK_A[k] - RK_B[k]) * q.r.dt;
+  a.b_dt32 = (float)a.b_dt;
+  a.amb_dt32 = (float)a.amb_dt;
   const int st = q.state;
   if (req_f64_registers(q.r.precision)) {
     double* S = r64(s, q, st);
