@@ -219,15 +219,22 @@ StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
       p.q_in = g->reg32[1]; p.dacc_in = A; p.dacc_out = A; p.q_out = nullptr;
     }
   } else {
+    // binary64 state S and accumulator A; the binary32 register `state` holds
+    // the binary32 copy of S (written by the previous step's last stage, whose
+    // stage output a_3 = b_3 makes exactly the narrowed new state, or by the
+    // calls that set the state), so every stage reads binary32 fields
     double* S = g->reg64[state];
     double* A = g->reg64[1 - state];
+    float* C = g->reg32[state];
+    float* D = g->reg32[1 - state];
     p.out64 = false;
+    p.in64 = false;
     if (k == 0) {
-      p.q_in = S; p.in64 = true; p.acc_in = S; p.acc_out = A; p.q_out = g->reg32[0];
+      p.q_in = C; p.acc_in = S; p.acc_out = A; p.q_out = D;
     } else if (k == 1) {
-      p.q_in = g->reg32[0]; p.in64 = false; p.acc_in = A; p.acc_out = A; p.q_out = g->reg32[1];
+      p.q_in = D; p.acc_in = A; p.acc_out = A; p.q_out = C;
     } else {
-      p.q_in = g->reg32[1]; p.in64 = false; p.acc_in = A; p.acc_out = A; p.q_out = nullptr;
+      p.q_in = C; p.acc_in = A; p.acc_out = A; p.q_out = D;  // D: the next state's binary32 copy
     }
   }
   return p;
@@ -426,6 +433,8 @@ int sbli_init_tgv(sbli_grid* g, double amplitude) {
     return SBLI_OK;
   }
   SBLI_TRY(launch_init_tgv(g->geom, g->params, amplitude, g->reg64[0], g->stream), "init_tgv launch");
+  if (g->precision == SBLI_FP32)
+    SBLI_TRY(launch_narrow(5 * g->geom.P, g->reg64[0], g->reg32[0], g->stream), "narrow launch");
   return SBLI_OK;
 }
 
@@ -446,6 +455,8 @@ int sbli_set_state(sbli_grid* g, const double* q, int q_is_host) {
     SBLI_TRY(launch_df_split(g->geom.P, g->ref, tmp, reinterpret_cast<float*>(g->reg64[dst]), g->stream), "df_split");
   } else {
     SBLI_TRY(launch_to_offset(g->geom, g->ref, tmp, g->reg64[dst], g->stream), "to_offset launch");
+    if (g->precision == SBLI_FP32)
+      SBLI_TRY(launch_narrow(5 * g->geom.P, g->reg64[dst], g->reg32[dst], g->stream), "narrow launch");
   }
   if (q_is_host) SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
   g->stages_done = 0;

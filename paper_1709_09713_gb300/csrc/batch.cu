@@ -89,16 +89,12 @@ cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int gr
     else batch_stage_kernel<float, float, float, 8, false, true, true><<<grid, TX * 8, smem, s>>>(p);
     return cudaGetLastError();
   }
-  static std::atomic<unsigned long long> d0{0}, d1{0}, d2{0};
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, double, float, 8, false, true>, smem, d0)) return e;
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, double, float, 8, true, true>, smem, d1)) return e;
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, false, true>, smem, d2)) return e;
-  if (in64) {
-    if (p.ke_items) batch_stage_kernel<float, double, float, 8, true, true><<<grid, TX * 8, smem, s>>>(p);
-    else batch_stage_kernel<float, double, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
-  } else {
-    batch_stage_kernel<float, float, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
-  }
+  if (in64) return cudaErrorInvalidValue;  // stages read the binary32 copy of the state
+  static std::atomic<unsigned long long> d0{0}, d1{0};
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, false, true>, smem, d0)) return e;
+  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, true, true>, smem, d1)) return e;
+  if (p.ke_items) batch_stage_kernel<float, float, float, 8, true, true><<<grid, TX * 8, smem, s>>>(p);
+  else batch_stage_kernel<float, float, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -264,11 +260,16 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
     else if (k == 1) { a.q_in = r32(0); a.dacc_in = A; a.dacc_out = A; a.q_out = r32(1); }
     else { a.q_in = r32(1); a.dacc_in = A; a.dacc_out = A; a.q_out = nullptr; }
   } else {
+    // binary64 state and accumulator; binary32 register `state` holds the
+    // binary32 copy of the state (as for single grids)
     double* S = r64(state);
     double* A = r64(1 - state);
-    if (k == 0) { a.q_in = S; *in64 = true; a.acc_in = S; a.acc_out = A; a.q_out = r32(0); }
-    else if (k == 1) { a.q_in = r32(0); *in64 = false; a.acc_in = A; a.acc_out = A; a.q_out = r32(1); }
-    else { a.q_in = r32(1); *in64 = false; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
+    float* Cs = r32(state);
+    float* Ds = r32(1 - state);
+    *in64 = false;
+    if (k == 0) { a.q_in = Cs; a.acc_in = S; a.acc_out = A; a.q_out = Ds; }
+    else if (k == 1) { a.q_in = Ds; a.acc_in = A; a.acc_out = A; a.q_out = Cs; }
+    else { a.q_in = Cs; a.acc_in = A; a.acc_out = A; a.q_out = Ds; }
   }
   return a;
 }
@@ -464,6 +465,10 @@ int sbli_batch_init_tgv(sbli_batch* b, const double* amplitudes) {
     SBLI_BTRY(launch_init_tgv(member_geom(M), b->params[m], amplitudes[m],
                               reinterpret_cast<double*>(b->reg64[0] + M.off64), b->stream),
               "init_tgv");
+    if (b->precision == SBLI_FP32)
+      SBLI_BTRY(launch_narrow(5 * M.P, reinterpret_cast<double*>(b->reg64[0] + M.off64),
+                              reinterpret_cast<float*>(b->reg32[0] + M.off32), b->stream),
+                "narrow");
   }
   return SBLI_OK;
 }
@@ -482,6 +487,9 @@ int sbli_batch_set_state(sbli_batch* b, int member, const double* q, int q_is_ho
               "df_split");
   } else {
     SBLI_BTRY(launch_to_offset(member_geom(M), make_ref(b->params[member]), tmp, dst, b->stream), "to_offset");
+    if (b->precision == SBLI_FP32)
+      SBLI_BTRY(launch_narrow(5 * M.P, dst, reinterpret_cast<float*>(b->reg32[b->state] + M.off32), b->stream),
+                "narrow");
   }
   if (q_is_host) SBLI_BTRY(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
   return SBLI_OK;

@@ -2,6 +2,7 @@
 // binary64 kinetic-energy / enstrophy reduction.
 #include <math.h>
 
+#include "fpconv.cuh"
 #include "sbli_internal.cuh"
 
 namespace sbli {
@@ -109,6 +110,18 @@ __global__ void widen_kernel(long long n, const float* __restrict__ src, double*
 
 cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_t s) {
   widen_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+// The binary32 copy of a binary64 state that stage 0 of the binary32 path
+// reads: the same narrowing the stage kernels apply (narrow_f64_fast).
+__global__ void narrow_kernel(long long n, const double* __restrict__ src, float* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = narrow_f64_fast(src[i]);
+}
+
+cudaError_t launch_narrow(long long n, const double* src, float* dst, cudaStream_t s) {
+  narrow_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
-// fused_fp32.cu -- binary32 instantiations of the fused stage kernel.  The
-// stage input is binary64 at stage 0 (the state between steps) and binary32
-// at stages 1-2; the accumulator is binary64 or, for the double-float mode,
-// a hi/lo binary32 pair.  Tiles 32 x 8 (two CTAs per SM) and 32 x 16 (one
+// fused_fp32.cu -- binary32 instantiations of the fused stage kernel.  Every
+// stage reads binary32 fields (stage 0 the binary32 copy of the state that the
+// previous step's last stage wrote); the accumulator is binary64 or, for the
+// double-float mode, a hi/lo binary32 pair.  The residual alone (RHS only)
+// may also read the binary64 state.  Tiles 32 x 8 (two CTAs per SM) and 32 x 16 (one
 // CTA of 16 warps per SM); the TMEM-queue and two-column kernels are in
 // their own files.
 #include "fused_stage.cuh"
@@ -15,10 +16,8 @@ static cudaError_t dispatch32(const StageArgs& a, const Coef<float>& c, bool in_
     if (in_fp64) return launch_fused_t<float, double, float, TY, true, false>(a, c, s);
     return launch_fused_t<float, float, float, TY, true, false>(a, c, s);
   }
-  if (in_fp64) {
-    if (a.ke_partials) return launch_fused_t<float, double, float, TY, false, true>(a, c, s);
-    return launch_fused_t<float, double, float, TY, false, false>(a, c, s);
-  }
+  if (in_fp64) return cudaErrorInvalidValue;  // stages read the binary32 copy of the state
+  if (a.ke_partials) return launch_fused_t<float, float, float, TY, false, true>(a, c, s);
   return launch_fused_t<float, float, float, TY, false, false>(a, c, s);
 }
 

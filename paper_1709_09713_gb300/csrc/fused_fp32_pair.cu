@@ -30,10 +30,8 @@ cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& cf, co
     if (a.ke_partials) return launch_fused_t<f32x2, float, float, 8, false, true, true>(a, c, s);
     return launch_fused_t<f32x2, float, float, 8, false, false, true>(a, c, s);
   }
-  if (in_fp64) {
-    if (a.ke_partials) return launch_fused_t<f32x2, double, float, 8, false, true>(a, c, s);
-    return launch_fused_t<f32x2, double, float, 8, false, false>(a, c, s);
-  }
+  if (in_fp64) return cudaErrorInvalidValue;  // stages read the binary32 copy of the state
+  if (a.ke_partials) return launch_fused_t<f32x2, float, float, 8, false, true>(a, c, s);
   return launch_fused_t<f32x2, float, float, 8, false, false>(a, c, s);
 }
 

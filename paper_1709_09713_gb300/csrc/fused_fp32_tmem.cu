@@ -18,10 +18,8 @@ static cudaError_t dispatch_tm(const StageArgs& a, const Coef<float>& c, bool in
     if (a.ke_partials) return launch_fused_t<float, float, float, TY, false, true, true, true>(a, c, s);
     return launch_fused_t<float, float, float, TY, false, false, true, true>(a, c, s);
   }
-  if (in_fp64) {
-    if (a.ke_partials) return launch_fused_t<float, double, float, TY, false, true, false, true>(a, c, s);
-    return launch_fused_t<float, double, float, TY, false, false, false, true>(a, c, s);
-  }
+  if (in_fp64) return cudaErrorInvalidValue;  // stages read the binary32 copy of the state
+  if (a.ke_partials) return launch_fused_t<float, float, float, TY, false, true, false, true>(a, c, s);
   return launch_fused_t<float, float, float, TY, false, false, false, true>(a, c, s);
 }
 

@@ -113,6 +113,8 @@ cudaError_t launch_from_offset(const Geom& g, const RefState& r, const double* q
                                cudaStream_t s);
 // dst[i] = (double)src[i], i < n
 cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_t s);
+// dst[i] = the binary32 narrowing of src[i] that the binary32 stage kernels apply
+cudaError_t launch_narrow(long long n, const double* src, float* dst, cudaStream_t s);
 // double-float register (5 hi fields, then 5 lo fields, binary32) <-> binary64
 // state (5 fields).  split: v = src - ref (fields 0 and 4), hi = (float)v,
 // lo = (float)(v - hi); join: dst = ((double)hi + (double)lo) + ref.  Pass a

@@ -177,11 +177,16 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
     else if (k == 1) { a.q_in = r32(s, q, 0); a.dacc_in = A; a.dacc_out = A; a.q_out = r32(s, q, 1); }
     else { a.q_in = r32(s, q, 1); a.dacc_in = A; a.dacc_out = A; a.q_out = nullptr; }
   } else {
+    // binary64 state and accumulator; binary32 register `st` holds the binary32
+    // copy of the state (as for single grids)
     double* S = r64(s, q, st);
     double* A = r64(s, q, 1 - st);
-    if (k == 0) { a.q_in = S; *in64 = true; a.acc_in = S; a.acc_out = A; a.q_out = r32(s, q, 0); }
-    else if (k == 1) { a.q_in = r32(s, q, 0); *in64 = false; a.acc_in = A; a.acc_out = A; a.q_out = r32(s, q, 1); }
-    else { a.q_in = r32(s, q, 1); *in64 = false; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
+    float* Cs = r32(s, q, st);
+    float* Ds = r32(s, q, 1 - st);
+    *in64 = false;
+    if (k == 0) { a.q_in = Cs; a.acc_in = S; a.acc_out = A; a.q_out = Ds; }
+    else if (k == 1) { a.q_in = Ds; a.acc_in = A; a.acc_out = A; a.q_out = Cs; }
+    else { a.q_in = Cs; a.acc_in = A; a.acc_out = A; a.q_out = Ds; }
   }
   return a;
 }
@@ -363,6 +368,7 @@ int sbli_server_tick(sbli_server* s, int* completed) {
                 "df_split");
     } else {
       SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 0), st), "init_tgv");
+      if (q.r.precision == SBLI_FP32) SBLI_STRY(launch_narrow(5 * q.P, r64(s, q, 0), r32(s, q, 0), st), "narrow");
     }
     s->active.push_back(q);
   }
