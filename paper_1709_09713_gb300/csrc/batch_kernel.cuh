@@ -21,7 +21,8 @@ struct BatchParams {
 };
 
 // One persistent launch of stage work for p.count members (grid = CTAs).
-// in64: the members' stage inputs are binary64 (binary32 path, stage 0);
+// in64: the members' stage inputs are binary64 (binary64-register kernels;
+// binary32 stages always read binary32 fields, so it must be false for them);
 // df: binary32 stages with the double-float accumulator (dacc pointers).
 template <typename T>
 cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStream_t s, bool df = false);
