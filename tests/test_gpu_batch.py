@@ -155,3 +155,23 @@ def test_batch_of_extreme_shapes_equals_single_grids(S, precision):
         assert torch.equal(b.get_state(m), g.get_state()), (m, n)
         g.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_batch_set_state_mid_run(S, precision):
+    """A member's state set after an odd number of steps (the other register
+    of the rotation) steps on exactly like a fresh single grid given it."""
+    sizes = [(24, 20, 16), (32, 16, 12)]
+    b = S.Batch(sizes, precision)
+    b.init_tgv([1.0, 0.9])
+    b.step_n(1, 1e-3)
+    e0 = 1.0 / (1.4 * 0.4 * 0.1**2) + 0.5
+    q = workloads.smooth_state(sizes[0], 77, offsets=(1.0, 0, 0, 0, e0), amplitudes=(0.05, 0.3, 0.3, 0.3, 0.3))
+    b.set_state(0, torch.from_numpy(q).cuda())
+    b.step_n(2, 1e-3)
+    g = S.Grid(sizes[0], precision, S.SBLI_FUSED)
+    g.set_state(torch.from_numpy(q).cuda())
+    g.step_n(2, 1e-3)
+    assert torch.equal(b.get_state(0), g.get_state())
+    g.close()
+    b.close()
