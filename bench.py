@@ -54,7 +54,7 @@ ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "d
 FUSED_FP64_FLOP_PER_PT = 572.1
 # DRAM bytes per launch, mean over the three stages of a step, from the ncu
 # captures summarised in profiles/ (an entry is removed once its kernel changes)
-NCU_TRAFFIC = {("fp64", 256): 2.249e9}
+NCU_TRAFFIC = {("fp64", 256): 2.252e9}
 # thread instructions per point-stage of the double-float kernel (ncu,
 # smsp__inst_executed x 32 / points); its ceiling is one warp instruction per
 # clock per SM sub-partition
