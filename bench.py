@@ -58,7 +58,7 @@ NCU_TRAFFIC = {("fp64", 256): 2.252e9}
 # thread instructions per point-stage of the double-float kernel (ncu,
 # smsp__inst_executed x 32 / points); its ceiling is one warp instruction per
 # clock per SM sub-partition
-DF64_INST_PER_PT = 3923.0
+DF64_INST_PER_PT = 3884.0
 
 
 def parse():
