@@ -1,10 +1,11 @@
 #!/usr/bin/env python3
 """Benchmark of the fused Navier-Stokes RHS + RK3 stage on GB300.
 
-Main workload: Taylor-Green vortex 256^3, binary64, Re 1600, M 0.1,
-dt 1e-3 (the paper's grid, §4 of arXiv:1709.09713), fused on-the-fly kernel.
-One bench step is one time step = 3 fused stages over the whole grid; the
-metric is point-stage updates per second.
+Main workload: Taylor-Green vortex 512^3, binary64, Re 1600, M 0.1,
+dt 5e-4 (the 512^3 single-solve workload; the paper's case of section 4 of
+arXiv:1709.09713 on a 512^3 grid), fused on-the-fly kernel.  One bench step is
+one time step = 3 fused stages over the whole grid; the metric is point-stage
+updates per second.
 
 The JSON line carries:
   value        device-resident throughput over exactly --steps steps (CUDA
@@ -13,12 +14,16 @@ The JSON line carries:
   e2e          the same metric through the public C ABI with host buffers:
                every e2e step copies the initial state from pinned host
                memory, runs --solve-steps time steps, copies the state back;
-  roofline     the fused stage kernel against its binding roofline (the FP64
-               pipe for binary64; HBM for the binary32 leg);
-  legs         the binary32-storage path at 512^3 (HBM roofline) and the
-               store-all comparison variant at 256^3;
+  roofline     the fused stage kernel against its binding roofline: the FP64
+               pipe for binary64, whose peak is measured in the same run by
+               the library's FMA-throughput probe (clocks sampled meanwhile);
+               HBM for the binary32 paths;
+  legs         binary32 storage at 512^3 (both accumulators, 200 steps, HBM
+               roofline), double-float arithmetic at 512^3, the paper's
+               algorithm classes (store-all BL ... SN2) at 256^3, the 64-member
+               ensemble and the serving traces;
   energy       NVML total-energy delta per point-stage over the timed region;
-  cpu_baseline the CPU oracle (unchanged) on a bounded sample.
+  cpu_baseline the CPU oracle (unchanged) on a bounded sample of the workload.
 ``--impl reference`` times only the CPU oracle (the reference arm).
 Multi-GPU (torchrun): independent replicas, one grid per rank (weak scaling).
 """
@@ -40,25 +45,47 @@ if ROOT not in sys.path:
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# binary64 peak derived from GB300's nominal 1.25 TFLOP/s: 152 SMs x 2 DFMA
-# (4 flop) per clock per SM x SM clock (2.07 GHz max) = 1.259 TFLOP/s
-FP64_FLOP_PER_CLK_PER_SM = 4.0
 
 # Algorithmic HBM bytes per point-stage of the fused kernel, averaged over
 # the three stages of a step (minimum traffic of the two-register scheme):
 #   binary64: 50 values per point-step / 3 * 8 B = 133.3 B
 #   binary32 stage fields + binary64 accumulator: 320 B / 3 = 106.7 B
 ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "df64": 400.0 / 3.0}
-# binary64 flop per point-stage the fused kernel executes (2 DFMA + DADD +
-# DMUL), counted by ncu on the three stages of a 256^3 step, mean (profiles/).
-FUSED_FP64_FLOP_PER_PT = 572.1
-# DRAM bytes per launch, mean over the three stages of a step, from the ncu
-# captures summarised in profiles/ (an entry is removed once its kernel changes)
-NCU_TRAFFIC = {("fp64", 256): 2.252e9}
-# thread instructions per point-stage of the double-float kernel (ncu,
-# smsp__inst_executed x 32 / points); its ceiling is one warp instruction per
-# clock per SM sub-partition
-DF64_INST_PER_PT = 3884.0
+
+# Counters of the stage kernels taken with ncu (profiles/), per point-stage,
+# each valid for the kernel sources whose hash is given (KERNEL_SOURCES under
+# paper_1709_09713_gb300/csrc); bench.py reports a counter as stale (null)
+# once the sources differ.
+#   fp64 flop_per_pt: binary64 flop executed (2 DFMA + DADD + DMUL), mean of
+#        the three stages of a 256^3 step; traffic_per_pt: DRAM read + write
+#        bytes per point of one launch, same capture (2.252e9 per launch at
+#        256^3; scaled by points to other grids);
+#   df64 inst_per_pt: thread instructions (smsp__inst_executed x 32 / points).
+KERNEL_SOURCES = ["fused_stage.cuh", "fused_fp64.cu", "fused_df64.cu", "dfloat.cuh", "fpconv.cuh", "f32x2.cuh",
+                  "sbli_internal.cuh"]
+KERNEL_COUNTS = {
+    "fp64": {"flop_per_pt": 572.1, "traffic_per_pt": 2.252e9 / 256**3, "sources": "844c6b84a261",
+             "profile": "profiles/fused_stage_fp64_256.md"},
+    "df64": {"inst_per_pt": 3884.0, "sources": "844c6b84a261", "profile": "profiles/fused_stage_df64_192.md"},
+}
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1709_09713_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def kernel_count(precision: str, key: str):
+    """A counter of KERNEL_COUNTS if it was taken on the current sources, else None."""
+    c = KERNEL_COUNTS.get(precision)
+    if not c or key not in c or c["sources"] != kernel_sources_hash():
+        return None
+    return c[key]
 
 
 def parse():
@@ -67,24 +94,28 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32df", "df64"],
                     help="main line precision: binary64 (default), binary32 storage with a binary64 or "
                          "double-float accumulator, or binary64 storage with double-float arithmetic")
     ap.add_argument("--variant", default="fused", choices=["fused", "store_all"])
     ap.add_argument("--alg-steps", type=int, default=24,
                     help="steps per algorithm class in the comparison leg (>= ~1 s each for NVML energy)")
-    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--dt", type=float, default=None,
+                    help="time step (default 5e-4 for n >= 512, the linear stability limit there, else 1e-3)")
     ap.add_argument("--solve-steps", type=int, default=10, help="time steps per e2e solve")
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--no-legs", action="store_true", help="skip the FP32 512^3 and store-all legs")
-    ap.add_argument("--leg-steps", type=int, default=20)
+    ap.add_argument("--leg-steps", type=int, default=200, help="time steps of the 512^3 binary32 legs")
+    ap.add_argument("--df64-leg-steps", type=int, default=40)
+    ap.add_argument("--ens-steps", type=int, default=40)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-nmax", type=int, default=128)
     ap.add_argument("--serve-steps-hi", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-n", type=int, default=64)
-    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample-planes", type=int, default=8,
+                    help="the oracle's bounded sample: a periodic n x n x planes slab of the workload's planes")
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--profile", choices=["stage", "algorithms", "ensemble"], default=None,
                     help="untimed runs for ncu: 'stage' = --steps steps of one grid (--n, --profile-precision, "
                          "--profile-variant) stage by stage; 'algorithms' = stage 0 of every binary64 "
@@ -94,7 +125,10 @@ def parse():
     ap.add_argument("--profile-precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--profile-variant", default="fused", choices=sorted(VARIANTS))
     ap.add_argument("--profile-config", default=None, help="tile_y,planes_per_cta,z_queue (default: the grid's)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.dt is None:
+        args.dt = 5e-4 if args.n >= 512 else 1e-3
+    return args
 
 
 def run_profile(args):
@@ -261,28 +295,67 @@ def weak_scaling_value(units_per_rank: float, seconds_this_rank: float) -> tuple
     return units_per_rank * ws / t, t
 
 
-def cpu_baseline(n: int, steps: int, dt: float):
-    """The CPU oracle, unchanged, on an n^3 TGV for `steps` time steps on all host cores."""
+def oracle_slab_sample(n: int, planes: int, steps: int, threads: int):
+    """The CPU oracle, unchanged, on a bounded sample of the n^3 workload: the
+    Taylor-Green vortex on a periodic n x n x `planes` slab (same points per
+    x2 plane and the same arithmetic per point as the full grid; `planes`/n
+    of its points), `steps` time steps on `threads` host threads.  Returns
+    (pt-stage/s, seconds, threads used)."""
     import oracle
 
     oracle.build()
-    oracle.set_threads(os.cpu_count() or 1)
-    p = oracle.params(n)
+    oracle.set_threads(threads)
+    p = oracle.params((n, n, planes))
     q = oracle.init_tgv(p)
     t0 = time.perf_counter()
-    oracle.step(p, q, dt, steps)
+    oracle.step(p, q, 1e-3, steps)
     el = time.perf_counter() - t0
+    return n * n * planes * 3 * steps / el, el, oracle.get_threads()
+
+
+def cpu_baseline(n: int, planes: int, steps: int):
+    """The oracle on all host cores, plus one time step of a narrower slab on one core."""
+    v, el, cores = oracle_slab_sample(n, planes, steps, os.cpu_count() or 1)
+    rows = max(5, n // 4)
+    v1, el1, _ = oracle_slab_sample_rows(n, rows, planes)
+    return {"value": v, "unit": "pt-stage/s", "cores": cores, "kind": "oracle",
+            "sample": f"TGV {n} x {n} x {planes} periodic slab (the {n}^3 workload's planes), FP64, {steps} time "
+                      f"steps ({3 * steps} stages) in {el:.2f} s",
+            "single_thread": {"value": v1, "unit": "pt-stage/s", "cores": 1,
+                              "sample": f"TGV {n} x {rows} x {planes} periodic slab, FP64, 1 time step in {el1:.2f} s"}}
+
+
+def oracle_slab_sample_rows(n: int, rows: int, planes: int):
+    """One time step of an n x rows x planes slab on one host thread."""
+    import oracle
+
+    oracle.build()
     cores = oracle.get_threads()
-    # the same oracle on one core, one time step
     oracle.set_threads(1)
+    p = oracle.params((n, rows, planes))
+    q = oracle.init_tgv(p)
     t0 = time.perf_counter()
-    oracle.step(p, q, dt, 1)
-    el1 = time.perf_counter() - t0
+    oracle.step(p, q, 1e-3, 1)
+    el = time.perf_counter() - t0
     oracle.set_threads(cores)
-    return {"value": n**3 * 3 * steps / el, "unit": "pt-stage/s", "cores": cores, "kind": "oracle",
-            "sample": f"TGV {n}^3 FP64, {steps} time steps ({3 * steps} stages) in {el:.2f} s",
-            "single_thread": {"value": n**3 * 3 / el1, "unit": "pt-stage/s", "cores": 1,
-                              "sample": f"TGV {n}^3 FP64, 1 time step in {el1:.2f} s"}}
+    return n * rows * planes * 3 / el, el, 1
+
+
+def probe_peak(S, precision, seconds, gpu_index):
+    """FMA throughput of this GPU (the library's probe), run for about
+    `seconds` with nvidia-smi clocks sampled meanwhile."""
+    import torch
+
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    rate, ms = S.sbli_probe_fma_rate(precision, 2000, sink.data_ptr())
+    iters = max(2000, int(2000 * seconds * 1e3 / max(ms, 1e-3)))
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    rate, ms = S.sbli_probe_fma_rate(precision, iters, sink.data_ptr())
+    clk = clocks.stop()
+    return {"flop_per_s": rate, "ms": ms, "iters": iters, "clocks": clk}
 
 
 def time_steps(S, g, stream, steps, dt, ws):
@@ -353,10 +426,14 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None, preci
     del b
     torch.cuda.empty_cache()
     acc = "f64 accumulator" if prec == S.SBLI_FP32 else "double-float accumulator"
+    peaks, kind = measured_peaks()
+    ach = ALG_BYTES["fp32"] * pts / (ms / (3 * steps) / 1e3) / 1e9
     return {"workload": f"ensemble of {count} TGV grids (N in {{32,48,64,96,128}}, Re U[100,1600], M U[0.1,0.4]), "
                         f"fp32 + {acc}, persistent launch per stage", "value": 3.0 * pts * steps * ws / (ms / 1e3),
             "unit": "pt-stage/s", "steps": steps, "points": pts, "work_items_per_stage": items,
-            "stage_ms": ms / (3 * steps), "launches_per_stage": 1, "energy": energy}
+            "stage_ms": ms / (3 * steps), "launches_per_stage": 1, "energy": energy,
+            "hbm": {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                    "peak_source": kind, "bytes_per_pt_stage": ALG_BYTES["fp32"]}}
 
 
 def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, arena_gb=200.0, fp64_as=0):
@@ -433,21 +510,23 @@ def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=N
     g.close()
     del g
     torch.cuda.empty_cache()
-    out = {"workload": f"TGV {n}^3 {precision} {variant}", "value": 3.0 * P * steps * ws / (ms / 1e3),
-           "unit": "pt-stage/s", "steps": steps, "stage_ms": stage_ms, "tile_y_planes": cfg,
-           "autotuned": bool(tune), "energy": energy}
+    out = {"workload": f"TGV {n}^3 {precision} {variant}, dt {dt}", "value": 3.0 * P * steps * ws / (ms / 1e3),
+           "unit": "pt-stage/s", "steps": steps, "stage_ms": stage_ms, "config": cfg,
+           "config_fields": "tile_y, planes_per_cta, z_queue, columns_per_thread", "autotuned": bool(tune),
+           "energy": energy}
     if variant == "fused":
         peaks, kind = measured_peaks()
         ach = ALG_BYTES[precision] * P / (stage_ms / 1e3) / 1e9
         out["hbm"] = {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                      "peak_source": kind}
-        if precision == "df64" and DF64_INST_PER_PT and clock_ghz:
+                      "peak_source": kind, "bytes_per_pt_stage": ALG_BYTES[precision]}
+        inst = kernel_count("df64", "inst_per_pt") if precision == "df64" else None
+        if inst and clock_ghz:
             sms = torch.cuda.get_device_properties(0).multi_processor_count
             peak = sms * 4 * 32 * clock_ghz * 1e9
-            rate = DF64_INST_PER_PT * P / (stage_ms / 1e3)
+            rate = inst * P / (stage_ms / 1e3)
             out["issue"] = {"achieved": rate, "peak": peak, "unit": "thread-instr/s", "frac": rate / peak,
-                            "note": f"{DF64_INST_PER_PT:.0f} instructions per pt-stage (ncu); peak = {sms} SMs x 4 "
-                                    f"sub-partitions x 32 lanes x {clock_ghz:.3f} GHz"}
+                            "note": f"{inst:.0f} instructions per pt-stage ({KERNEL_COUNTS['df64']['profile']}); "
+                                    f"peak = {sms} SMs x 4 sub-partitions x 32 lanes x {clock_ghz:.3f} GHz"}
     return out
 
 
@@ -489,6 +568,11 @@ def algorithms_leg(S, n, steps, warmup, dt, ws, nvml):
 
 # ------------------------------------------------------------- our arm
 
+def workload_name(args) -> str:
+    return (f"TGV {args.n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, Pr 0.71, gamma 1.4, "
+            f"dt {args.dt:g}")
+
+
 def run_ours(args):
     import torch
 
@@ -509,13 +593,17 @@ def run_ours(args):
     prec = PRECISIONS[args.precision]
     var = S.SBLI_FUSED if args.variant == "fused" else S.SBLI_STORE_ALL
     n, dt, P = args.n, args.dt, args.n**3
+
+    # the binary64 FMA peak of this GPU, measured now (the ALU roofline's denominator)
+    fp64_probe = probe_peak(S, S.SBLI_FP64, 1.0, local)
+
     stream = torch.cuda.Stream()
     g = S.Grid(n, prec, var, stream=stream)
-
     with torch.cuda.stream(stream):
         g.init_tgv(1.0)
         g.step_n(args.warmup, dt)
     stream.synchronize()
+    cfg = list(g.config()) if var == S.SBLI_FUSED else None
 
     nvml = Nvml(torch.cuda.current_device())
     clocks = ClockSampler(local)
@@ -529,8 +617,8 @@ def run_ours(args):
     stage_ms = ms / (3 * args.steps)  # one fused launch per stage
 
     # e2e: initial state from pinned host memory, --solve-steps steps, state back
-    q_host = torch.empty(g.shape, dtype=torch.float64).pin_memory()
-    r_host = torch.empty(g.shape, dtype=torch.float64).pin_memory()
+    q_host = torch.empty(g.shape, dtype=torch.float64, pin_memory=True)
+    r_host = torch.empty(g.shape, dtype=torch.float64, pin_memory=True)
     g.init_tgv(1.0)
     g.get_state(q_host)
     e2e_t = []
@@ -546,36 +634,41 @@ def run_ours(args):
     t_e2e = dist_max(min(e2e_t))
     state_bytes = 5 * P * 8
     g.close()
-    del g
+    del g, q_host, r_host
     torch.cuda.empty_cache()
 
     peaks, kind = measured_peaks()
+    src = kernel_sources_hash()
+    if prec in (S.SBLI_FP64, S.SBLI_DF64) and var == S.SBLI_FUSED:
+        hbm_frac = ALG_BYTES[args.precision] * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]
     if prec == S.SBLI_FP64 and var == S.SBLI_FUSED:
-        clock_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
-        sms = torch.cuda.get_device_properties(0).multi_processor_count
-        peak_tf = sms * FP64_FLOP_PER_CLK_PER_SM * clock_ghz / 1e3
-        ach = FUSED_FP64_FLOP_PER_PT * P / (stage_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
-                "traffic": NCU_TRAFFIC.get(("fp64", n)),
-                "note": f"binary64 pipe; {FUSED_FP64_FLOP_PER_PT:.0f} flop/pt-stage counted by ncu; peak = {sms} SMs x "
-                        f"4 flop/clk x {clock_ghz:.3f} GHz (median SM clock under load)",
-                "hbm_frac": ALG_BYTES["fp64"] * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
-    elif prec == S.SBLI_DF64 and var == S.SBLI_FUSED and DF64_INST_PER_PT:
+        flop = kernel_count("fp64", "flop_per_pt")
+        tpp = kernel_count("fp64", "traffic_per_pt")
+        peak_tf = fp64_probe["flop_per_s"] / 1e12
+        ach = flop * P / (stage_ms / 1e3) / 1e12 if flop else None
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf if ach else None, "traffic": tpp * P if tpp else None,
+                "note": f"binary64 FMA pipe; {flop} flop per pt-stage executed ({KERNEL_COUNTS['fp64']['profile']}, "
+                        f"kernel sources {KERNEL_COUNTS['fp64']['sources']}, current {src}); peak measured in this "
+                        f"run by sbli_probe_fma_rate (independent DFMA chains on every SM, "
+                        f"{fp64_probe['ms']:.0f} ms, median SM clock {fp64_probe['clocks'].get('sm_mhz')} MHz); "
+                        f"traffic = DRAM bytes per point of one 256^3 launch (ncu) x points",
+                "peak_source": "measured (probe, this run)", "hbm_frac": hbm_frac,
+                "hbm_peak_gbs": peaks["hbm_gbs"]}
+    elif prec == S.SBLI_DF64 and var == S.SBLI_FUSED:
+        inst = kernel_count("df64", "inst_per_pt")
         clock_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = sms * 4 * 32 * clock_ghz * 1e9
-        ach = DF64_INST_PER_PT * P / (stage_ms / 1e3)
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "thread-instr/s", "frac": ach / peak,
-                "traffic": None,
-                "note": f"binary32 issue: {DF64_INST_PER_PT:.0f} instructions per pt-stage (ncu); peak = {sms} SMs x "
-                        f"4 sub-partitions x 32 lanes x {clock_ghz:.3f} GHz",
-                "hbm_frac": ALG_BYTES["df64"] * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        ach = inst * P / (stage_ms / 1e3) if inst else None
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "thread-instr/s",
+                "frac": ach / peak if ach else None, "traffic": None,
+                "note": f"binary32 issue: {inst} instructions per pt-stage (ncu); peak = {sms} SMs x "
+                        f"4 sub-partitions x 32 lanes x {clock_ghz:.3f} GHz", "hbm_frac": hbm_frac}
     else:
-        pname = args.precision
-        ach = ALG_BYTES[pname] * P / (stage_ms / 1e3) / 1e9
+        ach = ALG_BYTES[args.precision] * P / (stage_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC.get((pname, n)) if var == S.SBLI_FUSED else None,
-                "peak_source": kind}
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": kind}
 
     line = {
         "metric": "pt-stage updates/s",
@@ -591,13 +684,16 @@ def run_ours(args):
         "dtype": {"fp64": "f64", "fp32": "f32 (f64 accumulator)", "fp32df": "f32 (f32-pair accumulator)",
                   "df64": "f32 pairs (double-float), f64 storage"}[args.precision],
         "data": "synthetic (Taylor-Green vortex initial field of section 4)",
-        "config": {"workload": f"TGV {n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, Pr 0.71, dt {dt}",
-                   "grid": [n, n, n], "l2": f"inputs larger than L2 ({state_bytes / 2**20:.0f} MiB state register)",
-                   "parallelism": f"independent replicas x{ws}"},
+        "config": {"workload": workload_name(args), "grid": [n, n, n],
+                   "l2": f"inputs larger than L2 ({state_bytes / 2**20:.0f} MiB state register)",
+                   "parallelism": f"independent replicas x{ws}", "launch_config": cfg,
+                   "launch_config_fields": "tile_y, planes_per_cta, z_queue, columns_per_thread"},
         "e2e": {"value": 3.0 * P * args.solve_steps * ws / t_e2e, "unit": "pt-stage/s",
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "note": f"each e2e step = H2D state + {args.solve_steps} time steps + D2H state"},
         "roofline": roof,
+        "fp64_peak_probe": {"tflops": fp64_probe["flop_per_s"] / 1e12, "ms": fp64_probe["ms"],
+                            "clocks": fp64_probe["clocks"]},
         "clocks": clk,
         "gpu_launches": 3 * args.steps,
         "stage_ms": stage_ms,
@@ -608,12 +704,12 @@ def run_ours(args):
                           "source": "nvmlDeviceGetTotalEnergyConsumption delta over the timed region"}
     if not args.no_legs:
         cg = (clk.get("sm_mhz") or 2070.0) / 1e3
-        line["legs"] = [leg(S, 256, "df64", "fused", args.leg_steps, 2, dt, ws, clock_ghz=cg, nvml=nvml),
-                        leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
+        line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
                         leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
-                        algorithms_leg(S, 256, args.alg_steps, 1, dt, ws, nvml),
-                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws, nvml=nvml),
-                        ensemble_leg(S, 2 * args.leg_steps, 6, dt, ws, nvml=nvml, precision=S.SBLI_FP32_DF),
+                        leg(S, 512, "df64", "fused", args.df64_leg_steps, 2, 5e-4, ws, clock_ghz=cg, nvml=nvml),
+                        algorithms_leg(S, 256, args.alg_steps, 1, 1e-3, ws, nvml),
+                        ensemble_leg(S, args.ens_steps, 6, 1e-3, ws, nvml=nvml),
+                        ensemble_leg(S, args.ens_steps, 6, 1e-3, ws, nvml=nvml, precision=S.SBLI_FP32_DF),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
                                     fp64_as=S.SBLI_DF64),
@@ -621,7 +717,7 @@ def run_ours(args):
                         serving_leg(S, args.serve_requests, 5.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
                                     fp64_as=S.SBLI_DF64)]
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_n, args.cpu_sample_steps, dt)
+        line["cpu_baseline"] = cpu_baseline(n, args.cpu_sample_planes, args.cpu_sample_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -629,7 +725,9 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    """The reference arm: the CPU oracle as it stands, on the host cores, on a
+    bounded sample of the main line's workload (an n x n x planes periodic
+    slab of its grid's planes per step)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -637,23 +735,27 @@ def run_reference(args):
 
     oracle.build()
     oracle.set_threads(os.cpu_count() or 1)
-    n = args.cpu_sample_n
-    p = oracle.params(n)
+    n, planes = args.n, args.cpu_sample_planes
+    p = oracle.params((n, n, planes))
     q = oracle.init_tgv(p)
     q = oracle.step(p, q, args.dt, args.warmup)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         q = oracle.step(p, q, args.dt, 1)
     el = time.perf_counter() - t0
-    value = 3.0 * n**3 * args.steps / el
+    pts = n * n * planes
+    value = 3.0 * pts * args.steps / el
+    sample = (f"each step: one time step of the Taylor-Green vortex on a periodic {n} x {n} x {planes} slab "
+              f"(the {n}^3 workload's points per x2 plane and arithmetic per point, {planes}/{n} of its points) "
+              f"on the CPU oracle")
     line = {
         "impl": "reference", "metric": "pt-stage updates/s", "value": value, "unit": "pt-stage/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Taylor-Green vortex of section 4)",
-        "config": {"workload": f"TGV {args.n}^3 {args.precision} {args.variant}, Re 1600, M 0.1, Pr 0.71, dt {args.dt}",
-                   "grid": [args.n] * 3, "sample": f"each step: one time step of the {n}^3 TGV on the CPU oracle"},
+        "config": {"workload": workload_name(args), "grid": [n, n, n], "sample": sample},
         "cpu_baseline": {"value": value, "unit": "pt-stage/s", "cores": oracle.get_threads(), "kind": "oracle",
-                         "sample": f"TGV {n}^3, {args.steps} time steps after {args.warmup} warm-up steps"},
+                         "sample": f"TGV {n} x {n} x {planes} slab, {args.steps} time steps after {args.warmup} "
+                                   f"warm-up steps"},
         "e2e": {"value": value, "unit": "pt-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

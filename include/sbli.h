@@ -193,11 +193,15 @@ SBLI_API int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev);
  * The partial sums live in one static device array of the library, 8192
  * pairs (128 KiB per GPU, held until the process exits); grids of more than
  * 8192 * 16384 = 134,217,728 points (512^3) are rejected with SBLI_EINVAL.
- * The first call on a device looks up that array's device address; make that
- * first call before any stream capture on the device.  Every call overwrites
- * the array (each partial sum is written before it is read, so nothing needs
- * clearing); calls that overlap on the GPU, on any streams, race on it and
- * must be ordered by the caller.  Asynchronous. */
+ * A call made while its stream is not being captured looks up that array's
+ * device address (again, so a device reset between calls is harmless); a call
+ * during stream capture reuses the address found by an earlier call on the
+ * device, so make the first call on each device before any stream capture
+ * (else SBLI_EINVAL).  q_dev and out_dev must be device or managed memory of
+ * the current device (else SBLI_EINVAL, nothing launched).  Every call
+ * overwrites the array (each partial sum is written before it is read, so
+ * nothing needs clearing); calls that overlap on the GPU, on any streams, race
+ * on it and must be ordered by the caller.  Asynchronous. */
 SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, int n2, double L, double* out_dev,
                                          void* stream);
 

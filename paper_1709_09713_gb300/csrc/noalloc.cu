@@ -17,6 +17,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "sbli_internal.cuh"
@@ -24,9 +25,10 @@
 namespace sbli {
 namespace {
 
-// Capacity of the static scratch in (ke, enstrophy) pairs, and the points
-// one block covers; together they bound the grid to
-// NOALLOC_MAX_PARTIALS * NOALLOC_POINTS_PER_BLOCK = 512^3 points.
+// Capacity of the static scratch in (ke, enstrophy) pairs (one per block),
+// and the most points one block may cover; together they bound the grid to
+// NOALLOC_MAX_PARTIALS * NOALLOC_POINTS_PER_BLOCK = 512^3 points.  A call
+// launches one block per NOALLOC_BLOCK points, at most NOALLOC_MAX_PARTIALS.
 constexpr int NOALLOC_MAX_PARTIALS = 8192;
 constexpr int NOALLOC_BLOCK = 256;
 constexpr long long NOALLOC_POINTS_PER_BLOCK = 64LL * NOALLOC_BLOCK;
@@ -34,25 +36,46 @@ constexpr long long NOALLOC_POINTS_PER_BLOCK = 64LL * NOALLOC_BLOCK;
 static __device__ __align__(256) double g_noalloc_partials[2 * NOALLOC_MAX_PARTIALS];
 
 // Device address of g_noalloc_partials per device (host code cannot use the
-// symbol itself: on the host it names a stand-in, not device memory).
+// symbol itself: on the host it names a stand-in, not device memory).  The
+// address is looked up again on every call made while the stream is not
+// being captured (so a device reset between calls is picked up); a call
+// during stream capture uses the address an earlier call stored.
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_ptr[MAX_DEVICES] = {};
 
-cudaError_t scratch_for_current_device(double** out) {
+cudaError_t scratch_for_current_device(cudaStream_t s, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;  // unknown: do not call into the runtime's module lookup
+  }
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = static_cast<double*>(p);
+  } else if (!g_scratch_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
+}
+
+// True when p is device (or managed) memory the current device can read.
+bool device_readable(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Same quantities as the workspace-based reduction, read from plain
@@ -127,24 +150,37 @@ extern "C" SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0,
                                                     double* out_dev, void* stream) {
   using namespace sbli;
   if (!q_dev || !out_dev) return noalloc_fail(SBLI_EINVAL, "q_dev and out_dev must be device pointers");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return noalloc_fail(SBLI_ECUDA, "no current CUDA device");
+  }
+  if (!device_readable(q_dev, dev) || !device_readable(out_dev, dev))
+    return noalloc_fail(SBLI_EINVAL, "q_dev and out_dev must be device (or managed) memory of the current device %d",
+                        dev);
   if (n0 < 5 || n1 < 5 || n2 < 5 || n0 > (1 << 24) || n1 > (1 << 24) || n2 > (1 << 24) ||
       (long long)n0 * n1 >= (1LL << 31))
     return noalloc_fail(SBLI_EINVAL, "grid %d x %d x %d: each edge must be in [5, 2^24] and n0*n1 < 2^31", n0, n1, n2);
   if (!(L > 0) || !isfinite(L)) return noalloc_fail(SBLI_EINVAL, "L must be finite and > 0");
   const long long P = (long long)n0 * n1 * n2;
-  const long long blocks = (P + NOALLOC_POINTS_PER_BLOCK - 1) / NOALLOC_POINTS_PER_BLOCK;
-  if (blocks > NOALLOC_MAX_PARTIALS)
+  if ((P + NOALLOC_POINTS_PER_BLOCK - 1) / NOALLOC_POINTS_PER_BLOCK > NOALLOC_MAX_PARTIALS)
     return noalloc_fail(SBLI_EINVAL,
                         "grid of %lld points exceeds the allocation-free maximum of %lld points "
                         "(static scratch of %d partial sums)",
                         P, (long long)NOALLOC_MAX_PARTIALS * NOALLOC_POINTS_PER_BLOCK, NOALLOC_MAX_PARTIALS);
+  // one block per NOALLOC_BLOCK points up to the scratch capacity; the
+  // kernel's grid-stride loop covers the rest
+  const long long blocks = std::min<long long>((P + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK, NOALLOC_MAX_PARTIALS);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
+  cudaError_t e = scratch_for_current_device(s, &scratch);
+  if (e == cudaErrorStreamCaptureUnsupported)
+    return noalloc_fail(SBLI_EINVAL, "first call on device %d made during stream capture: call once before capturing",
+                        dev);
   if (e != cudaSuccess) return noalloc_fail(SBLI_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
   sbli_params prm{1.0, 1.0, 1.0, 1.4, L};
   const int n[3] = {n0, n1, n2};
   const Geom g{n0, n1, n2, P};
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   ke_plain_kernel<<<(unsigned)blocks, NOALLOC_BLOCK, 0, s>>>(g, make_coef<double>(n, prm), q_dev, scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(SBLI_ECUDA, "kernel launch: %s", cudaGetErrorString(e));

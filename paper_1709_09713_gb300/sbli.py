@@ -93,6 +93,7 @@ SIGNATURES = {
     "sbli_server_poll": (_c_int, [_vp, ctypes.POINTER(Result), _c_int, ctypes.POINTER(_c_int)]),
     "sbli_server_stats": (_c_int, [_vp, ctypes.POINTER(ServerStatus)]),
     "sbli_last_error": (ctypes.c_char_p, []),
+    "sbli_probe_fma_rate": (_c_int, [_c_int, ctypes.c_longlong, _vp, _vp, _DP, ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lock = threading.Lock()
@@ -204,6 +205,14 @@ def sbli_kinetic_energy_noalloc(q_ptr: int, n0: int, n1: int, n2: int, L: float,
                                 stream: int = 0) -> None:
     """Allocation-free KE/enstrophy of a plain device state (no grid, no workspace)."""
     _check(lib().sbli_kinetic_energy_noalloc(_vp(q_ptr), n0, n1, n2, float(L), _vp(out_ptr), _vp(stream)))
+
+
+def sbli_probe_fma_rate(precision: int, iters: int, sink_ptr: int, stream: int = 0) -> tuple[float, float]:
+    """FMA throughput of the current device (include/sbli_probe.h): (flop/s, kernel ms)."""
+    rate, ms = _c_double(), ctypes.c_float()
+    _check(lib().sbli_probe_fma_rate(int(precision), int(iters), _vp(sink_ptr), _vp(stream), ctypes.byref(rate),
+                                     ctypes.byref(ms)))
+    return rate.value, ms.value
 
 
 def sbli_get_config(h: int) -> tuple[int, int, int, int]:

@@ -1,6 +1,6 @@
 """CPU-side checks of the C ABI: the library loads without a GPU, exports
-every entry point include/sbli.h declares, and rejects invalid arguments
-that need no device."""
+every entry point the headers under include/ declare, and rejects invalid
+arguments that need no device."""
 import ctypes
 import os
 import re
@@ -22,7 +22,8 @@ def sbli():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "sbli.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"SBLI_API\s+(?:const\s+)?\w+\*?\s+\*?(sbli_\w+)\s*\(", text)))
 
 
@@ -184,3 +185,16 @@ def test_batch_limits(sbli):
         assert e.value.code == sbli.SBLI_EINVAL
     lib = sbli.lib()
     assert lib.sbli_batch_workspace_bytes(0, None, 1, None) == sbli.SBLI_EINVAL
+
+
+def test_probe_rejects_arguments_without_a_device(sbli):
+    """The throughput probe checks its arguments before touching a device."""
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_probe_fma_rate(sbli.SBLI_DF64, 10, 1)
+    assert e.value.code == sbli.SBLI_EINVAL
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_probe_fma_rate(sbli.SBLI_FP64, 0, 1)
+    assert e.value.code == sbli.SBLI_EINVAL
+    with pytest.raises(sbli.SbliError) as e:
+        sbli.sbli_probe_fma_rate(sbli.SBLI_FP64, 10, 0)
+    assert e.value.code == sbli.SBLI_EINVAL

@@ -89,3 +89,60 @@ def test_noalloc_rejects_grids_beyond_its_maximum(S):
     assert e.value.code == S.SBLI_EINVAL
     with pytest.raises(S.SbliError):
         S.sbli_kinetic_energy_noalloc(0, 8, 8, 8, 1.0, out.data_ptr())
+
+
+def test_noalloc_domain_scale_and_side_stream(S):
+    """L = 2 doubles every spacing h: the kinetic energy is unchanged and the
+    enstrophy (squares of first derivatives) scales by exactly 1/4 in
+    binary arithmetic; the result does not depend on the stream used."""
+    n = (24, 20, 28)
+    q = _state(n, 303)
+    base = _noalloc(S, n, q, L=1.0)
+    scaled = _noalloc(S, n, q, L=2.0)
+    assert scaled[0] == pytest.approx(base[0], rel=1e-15)
+    assert scaled[1] == pytest.approx(base[1] / 4.0, rel=1e-13)
+    side = torch.cuda.Stream()
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    S.sbli_kinetic_energy_noalloc(q.data_ptr(), n[0], n[1], n[2], 1.0, out.data_ptr(), side.cuda_stream)
+    side.synchronize()
+    assert np.array_equal(out.cpu().numpy(), base)
+
+
+def test_noalloc_limit_and_pointers_checked_before_launch(S):
+    """One plane past 512^3 is refused, as are host pointers, with nothing
+    launched (the output keeps its sentinel)."""
+    q = torch.zeros(16, dtype=torch.float64, device="cuda")
+    out = torch.full((2,), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(S.SbliError) as e:
+        S.sbli_kinetic_energy_noalloc(q.data_ptr(), 512, 512, 513, 1.0, out.data_ptr())
+    assert e.value.code == S.SBLI_EINVAL
+    host = np.zeros(5 * 8 * 8 * 8)
+    with pytest.raises(S.SbliError) as e:
+        S.sbli_kinetic_energy_noalloc(host.ctypes.data, 8, 8, 8, 1.0, out.data_ptr())
+    assert e.value.code == S.SBLI_EINVAL
+    hout = np.zeros(2)
+    qd = _state((8, 8, 8), 5)
+    with pytest.raises(S.SbliError) as e:
+        S.sbli_kinetic_energy_noalloc(qd.data_ptr(), 8, 8, 8, 1.0, hout.ctypes.data)
+    assert e.value.code == S.SBLI_EINVAL
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == [7.0, 7.0]
+
+
+def test_noalloc_allocates_nothing(S):
+    """After a first call (module and symbol set-up), further calls leave the
+    device's free memory and torch's allocation count unchanged."""
+    n = (32, 32, 32)
+    q = _state(n, 404)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    S.sbli_kinetic_energy_noalloc(q.data_ptr(), n[0], n[1], n[2], 1.0, out.data_ptr())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(5):
+        S.sbli_kinetic_energy_noalloc(q.data_ptr(), n[0], n[1], n[2], 1.0, out.data_ptr())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
