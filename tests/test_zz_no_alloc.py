@@ -7,6 +7,8 @@ device array.  These checks call it through the C ABI and compare it with the
 workspace-based sbli_kinetic_energy on the same states, twice in a row (the
 static array is shared by every call and keeps the previous call's sums).
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -138,6 +140,7 @@ def test_noalloc_allocates_nothing(S):
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     S.sbli_kinetic_energy_noalloc(q.data_ptr(), n[0], n[1], n[2], 1.0, out.data_ptr())
     torch.cuda.synchronize()
+    gc.collect()  # tensors of earlier tests freed now, not during the loop below
     free0, _ = torch.cuda.mem_get_info()
     alloc0 = torch.cuda.memory_allocated()
     for _ in range(5):
