@@ -124,7 +124,8 @@ namespace {
 // CTAs per SM a tile height allows (shared memory bound).
 int ctas_per_sm(int precision, int ty, int px = 1, int zq = 0) {
   if (f64_registers(precision) || ty >= 16 || px == 2) return 1;
-  return zq ? 3 : 2;  // the TMEM z queue keeps 3 full-record planes in shared memory
+  if (zq == 2) return 2;  // two planes per thread: two pair-record slots (83 KiB)
+  return zq ? 3 : 2;      // the TMEM z queue keeps 3 full-record planes in shared memory
 }
 
 // Planes per CTA ranked by a wave-balance model: cost = waves * (zc + 1.5),
@@ -173,7 +174,8 @@ FusedConfig default_config(const Geom& g, int precision) {
 }
 
 bool valid_config(int precision, int ty, int zc, int zq = 0, int px = 1) {
-  if (zc < 4 || zq < 0 || zq > 1 || px < 1 || px > 2) return false;
+  if (zc < 4 || zq < 0 || zq > 2 || px < 1 || px > 2) return false;
+  if (zq == 2) return !f64_registers(precision) && ty == 8 && px == 1;  // two planes per thread, 32 x 8
   if (f64_registers(precision)) return ty == 8 && px == 1;  // shared-memory ring or TMEM queue
   if (px == 2) return ty == 8 && zq == 0;  // 64 x 8 two-column tiles, shared-memory ring
   return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
@@ -699,7 +701,7 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int*
   int nc = 0;
   const int tys[2] = {8, 16};
   for (int px = 1; px <= 2; ++px)
-    for (int zq = 0; zq < 2; ++zq)
+    for (int zq = 0; zq <= 2; ++zq)
       for (int t = 0; t < 2; ++t) {
         if (!valid_config(g->precision, tys[t], 4, zq, px)) continue;
         int zc[3];

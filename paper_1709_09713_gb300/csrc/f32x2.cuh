@@ -11,7 +11,7 @@
 
 namespace sbli {
 
-struct f32x2 {
+struct __align__(8) f32x2 {  // 8-byte aligned: one 64-bit register pair, one 8-byte access
   float x, y;
   f32x2() = default;
   __host__ __device__ constexpr f32x2(float a, float b) : x(a), y(b) {}

@@ -559,6 +559,31 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
   t.G[A] = fma(c.e0[A], uc[A], lAA + gA);  // D2_A u_A + D1_A s_A (Eq. 7 on j = A, D1 o D1 otherwise)
 }
 
+// Eqs. 1-3 at one point from the accumulated derivative terms and the
+// centre values (deviation form: rho' = rho - 1, E' = rho E - (rho E)_ref).
+template <typename T>
+__device__ __forceinline__ void assemble_residual(const Terms<T>& t, T rho_p, const T (&mc)[3], T Ec, const T (&uc)[3],
+                                                  T Tc, const Coef<T>& c, T (&R)[5]) {
+  const T e0sum = c.e0[0] + c.e0[1] + c.e0[2];  // centre coefficient of the Laplacian
+  const T div = t.g[0][0] + t.g[1][1] + t.g[2][2];
+  const T rho = T(1) + rho_p;
+  R[0] = T(-0.5) * mad(rho, div, t.rrho);
+  T uvisc = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T lap = fma(e0sum, uc[i], t.lap[i]);
+    const T visc = mad(t.G[i], T(1.0 / 3.0), lap);  // Laplacian + G - (2/3) G
+    uvisc = mad(uc[i], visc, uvisc);
+    R[1 + i] = mad(c.inv_re, visc, T(-0.5) * mad(mc[i], div, t.rM[i]));
+  }
+  // viscous dissipation du_i/dx_j (du_i/dx_j + du_j/dx_i - 2/3 div delta_ij)
+  const T a01 = t.g[0][1] + t.g[1][0], a02 = t.g[0][2] + t.g[2][0], a12 = t.g[1][2] + t.g[2][1];
+  const T sq = mad(t.g[2][2], t.g[2][2], mad(t.g[1][1], t.g[1][1], t.g[0][0] * t.g[0][0]));
+  const T diss = mad(T(2), sq, mad(a12, a12, mad(a02, a02, mad(a01, a01, T(-2.0 / 3.0) * div * div))));
+  const T lapT = fma(e0sum, Tc, t.lapT);
+  R[4] = mad(c.kappa, lapT, mad(c.inv_re, uvisc + diss, mad(-c.H0, div, T(-0.5) * mad(Ec, div, t.rE))));
+}
+
 template <int A, typename T, typename LD, typename SF>
 __device__ __forceinline__ void axis_terms_any(const LD& ldrec, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
                                                Terms<T>& t) {
@@ -710,8 +735,10 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   for (int k = 0; k < (ZT ? NFULL : 1); ++k) rf[k] = (k + 1) % (ZT ? NFULL : 1);
 
   TIN pf[LPT][NF][PP];
-  auto issue_loads = [&](int it_load) {
-    const unsigned zoff = (unsigned)wrapi(zbeg - HALO + it_load, n2) * plane;
+  int zl = wrapi(zbeg - HALO, n2);  // next plane to load (periodic), advanced one plane per load
+  auto issue_loads = [&]() {
+    const unsigned zoff = (unsigned)zl * plane;
+    zl = (zl + 1 == n2) ? 0 : zl + 1;
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
       if (l == 0 || ld_off[l][0] >= 0) {  // the own point always exists
@@ -724,7 +751,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       }
     }
   };
-  issue_loads(0);
+  issue_loads();
 
   for (int it = 0; it < nit; ++it) {
     // ---------------------------------------------------------------- phase 1
@@ -778,7 +805,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         }
       }
     }
-    if (it + 1 < nit) issue_loads(it + 1);
+    if (it + 1 < nit) issue_loads();
     __syncthreads();
     // --------------------------------------------------------------- phase 2a
     // in-plane diagonal gradients of the entering plane, kept for s_2 and
@@ -930,26 +957,9 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         axis_terms_any<2>(ld, sf, c, uc, t);
       }
 
-      // assemble Eqs. 1-3
-      const T e0sum = c.e0[0] + c.e0[1] + c.e0[2];  // centre coefficient of the Laplacian
-      const T div = t.g[0][0] + t.g[1][1] + t.g[2][2];
       const T rho = T(1) + rho_p;
       T R[5];
-      R[0] = T(-0.5) * mad(rho, div, t.rrho);
-      T uvisc = T(0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const T lap = fma(e0sum, uc[i], t.lap[i]);
-        const T visc = mad(t.G[i], T(1.0 / 3.0), lap);  // Laplacian + G - (2/3) G
-        uvisc = mad(uc[i], visc, uvisc);
-        R[1 + i] = mad(c.inv_re, visc, T(-0.5) * mad(mc[i], div, t.rM[i]));
-      }
-      // viscous dissipation du_i/dx_j (du_i/dx_j + du_j/dx_i - 2/3 div delta_ij)
-      const T a01 = t.g[0][1] + t.g[1][0], a02 = t.g[0][2] + t.g[2][0], a12 = t.g[1][2] + t.g[2][1];
-      const T sq = mad(t.g[2][2], t.g[2][2], mad(t.g[1][1], t.g[1][1], t.g[0][0] * t.g[0][0]));
-      const T diss = mad(T(2), sq, mad(a12, a12, mad(a02, a02, mad(a01, a01, T(-2.0 / 3.0) * div * div))));
-      const T lapT = fma(e0sum, Tc, t.lapT);
-      R[4] = mad(c.kappa, lapT, mad(c.inv_re, uvisc + diss, mad(-c.H0, div, T(-0.5) * mad(Ec, div, t.rE))));
+      assemble_residual(t, rho_p, mc, Ec, uc, Tc, c, R);
 
 #pragma unroll
       for (int j = 0; j < PP; ++j) {

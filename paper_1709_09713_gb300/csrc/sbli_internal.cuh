@@ -80,7 +80,9 @@ struct FusedConfig {
   int ty;  // in-plane tile height (tile is 32 x ty)
   int zc;  // planes per CTA
   int zq;  // binary32 paths: 0 = x2-neighbour records from the shared-memory
-           // ring, 1 = from a per-thread queue in tensor memory (TMEM)
+           // ring, 1 = from a per-thread queue in tensor memory (TMEM),
+           // 2 = TMEM queue with two x2 planes per thread computed together
+           // in packed FP32x2 instructions (stages only; 32 x 8 tiles)
   int px;  // binary32 paths: columns per thread (1, or 2 = columns x and x + 32
            // of a 64 x ty tile computed together)
 };
@@ -104,6 +106,9 @@ cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& c, con
 // the same two binary32 paths with the TMEM z queue (fused_fp32_tmem.cu)
 cudaError_t launch_fused_fp32_tmem(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                                    bool df, bool rhs_only, cudaStream_t s);
+// the two binary32 paths with two x2 planes per thread (fused_fp32_zpair.cu)
+cudaError_t launch_fused_fp32_zpair(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool df,
+                                    cudaStream_t s);
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg);
 
 // Diagnostics and state conversion (diag.cu).
