@@ -215,13 +215,10 @@ SBLI_API int sbli_kinetic_energy_noalloc(const double* q_dev, int n0, int n1, in
  * and, for binary32 grids, how many columns each thread owns
  * (columns_per_thread = 1, or 2: columns x and x + 32 of a 64 x 8 tile
  * computed together in packed two-lane FP32 instructions; shared-memory
- * ring only).  z_queue = 2 (binary32 grids, tile_y 8, one column per thread):
- * the TMEM queue with two consecutive x2 planes per thread computed together
- * in packed two-lane FP32 instructions (stages; the residual alone of such a
- * grid runs the z_queue = 1 kernel).  Tile height, planes per CTA and
- * z_queue 0/1 give bitwise the same state; two columns or two planes per
- * thread fuse multiply-adds differently (each bitwise equal among its own
- * configurations, within the binary32 tolerance of one column).  set_config validates and applies it
+ * ring only).  Tile height, planes
+ * per CTA and z_queue give bitwise the same state; two columns per thread
+ * fuse multiply-adds differently (bitwise equal among themselves, within the
+ * binary32 tolerance of one column).  set_config validates and applies it
  * (cached step graphs are rebuilt); must be called at a step boundary.
  * z_queue and columns_per_thread may be NULL in get_config. */
 SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_cta, int* z_queue,

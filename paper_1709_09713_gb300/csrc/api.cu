@@ -124,8 +124,7 @@ namespace {
 // CTAs per SM a tile height allows (shared memory bound).
 int ctas_per_sm(int precision, int ty, int px = 1, int zq = 0) {
   if (f64_registers(precision) || ty >= 16 || px == 2) return 1;
-  if (zq == 2) return 2;  // two planes per thread: two pair-record slots (83 KiB)
-  return zq ? 3 : 2;      // the TMEM z queue keeps 3 full-record planes in shared memory
+  return zq ? 3 : 2;  // the TMEM z queue keeps 3 full-record planes in shared memory
 }
 
 // Planes per CTA ranked by a wave-balance model: cost = waves * (zc + 1.5),
@@ -174,8 +173,7 @@ FusedConfig default_config(const Geom& g, int precision) {
 }
 
 bool valid_config(int precision, int ty, int zc, int zq = 0, int px = 1) {
-  if (zc < 4 || zq < 0 || zq > 2 || px < 1 || px > 2) return false;
-  if (zq == 2) return !f64_registers(precision) && ty == 8 && px == 1;  // two planes per thread, 32 x 8
+  if (zc < 4 || zq < 0 || zq > 1 || px < 1 || px > 2) return false;
   if (f64_registers(precision)) return ty == 8 && px == 1;  // shared-memory ring or TMEM queue
   if (px == 2) return ty == 8 && zq == 0;  // 64 x 8 two-column tiles, shared-memory ring
   return ty == 8 || ty == 16;  // binary32 stage fields (either accumulator)
@@ -265,6 +263,7 @@ cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_
     a.ke_partials = ke_partials;
     a.dacc_in = p.dacc_in;
     a.dacc_out = p.dacc_out;
+    a.df_normalize = (k == 2);
     if (g->precision == SBLI_FP64) return launch_fused_fp64(a, g->cd, g->cfg, false, s);
     if (g->precision == SBLI_DF64) return launch_fused_df64(a, g->cw, g->cfg, false, s);
     if (g->precision == SBLI_FP32_DF) return launch_fused_fp32df(a, g->cf, g->cfg, false, s);
@@ -701,7 +700,7 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int*
   int nc = 0;
   const int tys[2] = {8, 16};
   for (int px = 1; px <= 2; ++px)
-    for (int zq = 0; zq <= 2; ++zq)
+    for (int zq = 0; zq < 2; ++zq)
       for (int t = 0; t < 2; ++t) {
         if (!valid_config(g->precision, tys[t], 4, zq, px)) continue;
         int zc[3];

@@ -241,6 +241,7 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
   a.amb_dt = (RK_A[k] - RK_B[k]) * dt;
   a.b_dt32 = (float)a.b_dt;
   a.amb_dt32 = (float)a.amb_dt;
+  a.df_normalize = (k == 2);
   auto r64 = [&](int r) { return reinterpret_cast<double*>(b->reg64[r] + M.off64); };
   auto r32 = [&](int r) { return reinterpret_cast<float*>(b->reg32[r] + M.off32); };
   if (batch_f64_registers(b->precision)) {

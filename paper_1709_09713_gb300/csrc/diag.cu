@@ -21,6 +21,8 @@ Coef<T> make_coef(const int n[3], const sbli_params& p) {
   const double inv_re = isinf(p.Re) ? 0.0 : 1.0 / p.Re;
   c.gm1 = T(p.gamma - 1.0);
   c.gM2 = T(p.gamma * p.Mach * p.Mach);
+  c.gm1x2 = T(2.0 * (p.gamma - 1.0));
+  c.hgM2 = T(0.5 * p.gamma * p.Mach * p.Mach);
   c.inv_re = T(inv_re);
   c.kappa = T(inv_re / ((p.gamma - 1.0) * p.Mach * p.Mach * p.Pr));
   c.H0 = T(1.0 / ((p.gamma - 1.0) * p.Mach * p.Mach));

@@ -3,9 +3,8 @@
 // previous step's last stage wrote); the accumulator is binary64 or, for the
 // double-float mode, a hi/lo binary32 pair.  The residual alone (RHS only)
 // may also read the binary64 state.  Tiles 32 x 8 (two CTAs per SM) and 32 x 16 (one
-// CTA of 16 warps per SM); the TMEM-queue, two-column and two-plane kernels
-// are in their own files (the residual alone of a two-plane configuration
-// runs the one-plane TMEM-queue kernel).
+// CTA of 16 warps per SM); the TMEM-queue and two-column kernels are in
+// their own files.
 #include "fused_stage.cuh"
 
 namespace sbli {
@@ -25,7 +24,6 @@ static cudaError_t dispatch32(const StageArgs& a, const Coef<float>& c, bool in_
 cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                               bool rhs_only, cudaStream_t s) {
   if (cfg.px == 2) return launch_fused_fp32_pair(a, c, cfg, in_fp64, false, rhs_only, s);
-  if (cfg.zq == 2 && !rhs_only && !in_fp64) return launch_fused_fp32_zpair(a, c, cfg, false, s);
   if (cfg.zq) return launch_fused_fp32_tmem(a, c, cfg, in_fp64, false, rhs_only, s);
   switch (cfg.ty) {
     case 8: return dispatch32<8>(a, c, in_fp64, rhs_only, s);
@@ -44,7 +42,6 @@ static cudaError_t dispatch32df(const StageArgs& a, const Coef<float>& c, bool r
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s) {
   if (cfg.px == 2) return launch_fused_fp32_pair(a, c, cfg, false, true, rhs_only, s);
-  if (cfg.zq == 2 && !rhs_only) return launch_fused_fp32_zpair(a, c, cfg, true, s);
   if (cfg.zq) return launch_fused_fp32_tmem(a, c, cfg, false, true, rhs_only, s);
   switch (cfg.ty) {
     case 8: return dispatch32df<8>(a, c, rhs_only, s);

@@ -19,6 +19,8 @@ cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& cf, co
   }
   c.gm1 = f32x2(cf.gm1, cf.gm1);
   c.gM2 = f32x2(cf.gM2, cf.gM2);
+  c.gm1x2 = f32x2(cf.gm1x2, cf.gm1x2);
+  c.hgM2 = f32x2(cf.hgM2, cf.hgM2);
   c.inv_re = f32x2(cf.inv_re, cf.inv_re);
   c.kappa = f32x2(cf.kappa, cf.kappa);
   c.H0 = f32x2(cf.H0, cf.H0);

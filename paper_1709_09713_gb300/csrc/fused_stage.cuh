@@ -17,8 +17,8 @@
 //     conserved variables loaded from HBM (periodic wrap in the index
 //     arithmetic replaces the boundary pass of Fig. 1);
 //   * the loads of the next entering plane are issued as soon as the current
-//     plane is stored, and the centre plane's accumulator values after the
-//     x0 terms, so HBM latency overlaps the arithmetic;
+//     plane is stored, and the centre plane's accumulator values as its
+//     derivative terms start, so HBM latency overlaps the arithmetic;
 //   * x0/x1 derivatives read the centre slot, x2 derivatives read the ring;
 //     each axis streams its four neighbour records through the accumulators
 //     one at a time (axis_terms_stream; the double-float type keeps the
@@ -65,7 +65,10 @@ constexpr int HALO = 2;
 constexpr int SX = TX + 2 * HALO;
 constexpr int NSLOT = 5;
 
-// primitive values of one point record in a ring slot
+// primitive values of one point record in a ring slot; V_P holds 2 p' (the
+// pressure enters Eqs. 2-3 only as 2 D_i p and 2 D_j(p u_j) in the combined
+// skew form, so the factor 2 is applied once per point instead of once per
+// stencil neighbour; scaling by 2 is exact)
 enum { V_RHO, V_M0, V_M1, V_M2, V_E, V_U0, V_U1, V_U2, V_P, V_T, NV };
 
 // ZT (binary32 with the TMEM z queue): the x2 neighbours of a thread's own
@@ -480,8 +483,8 @@ __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, cons
   const T mY1 = -Y1, mX2 = -X2;
 #pragma unroll
   for (int i = 0; i < 3; ++i) t.rM[i] += d1w(V_M0 + i);
-  t.rM[A] = mad(T(2), SBLI_D1(V_P), t.rM[A]);
-  t.rE += mad(T(2), mad(r[0][V_P], Y2, mad(r[3][V_P], mX2, mad(r[1][V_P], mY1, r[2][V_P] * X1))), d1w(V_E));
+  t.rM[A] = t.rM[A] + SBLI_D1(V_P);  // D_A (2 p')
+  t.rE += mad(r[0][V_P], Y2, mad(r[3][V_P], mX2, mad(r[1][V_P], mY1, r[2][V_P] * X1))) + d1w(V_E);
   t.rrho += d1(fma(ua, r[0][V_RHO], r[0][V_M0 + A]), fma(ua, r[1][V_RHO], r[1][V_M0 + A]),
                fma(ua, r[2][V_RHO], r[2][V_M0 + A]), fma(ua, r[3][V_RHO], r[3][V_M0 + A]));
 #pragma unroll
@@ -513,33 +516,23 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
   T lAA = T(0);                       // sum_k e_k u_A,k: D2_A u_A without its centre term
   T gA = T(0);                        // sum_k c_k s_k = D1_A s_A
   T gI[3] = {T(0), T(0), T(0)};      // D1_A u_i, i != A
-  // binary64 (bound by its FMA pipe): the per-axis products c u_A^c and the
-  // doubled weights 2c once, so each neighbour's weights are one FMA / one
-  // multiply; binary32 keeps the register-leaner per-neighbour form
-  constexpr bool PRE = std::is_same<T, double>::value;
-  const T cu1 = PRE ? c1 * ua : T(0), cu2 = PRE ? c2 * ua : T(0);
-  const T c1x2 = PRE ? c1 + c1 : T(0), c2x2 = PRE ? c2 + c2 : T(0);
+  // the per-axis products c u_A^c once, so that each neighbour's two
+  // weights are one multiply and one fused multiply-add
+  const T cu1 = c1 * ua, cu2 = c2 * ua;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const T cd = (k == 0) ? c2 : (k == 1) ? -c1 : (k == 2) ? c1 : -c2;
     const T ed = (k == 0 || k == 3) ? e2 : e1;
+    const T cdu = (k == 0) ? cu2 : (k == 1) ? -cu1 : (k == 2) ? cu1 : -cu2;
     T r[NV];
     ldrec(k, r);
     const T sk = sfun(k, r);
-    T w, cd2;
-    if constexpr (PRE) {
-      const T cdu = (k == 0) ? cu2 : (k == 1) ? -cu1 : (k == 2) ? cu1 : -cu2;
-      w = fma(cd, r[V_U0 + A], cdu);            // D1(f (u_A + u_A^c)) weight
-      cd2 = (k == 0) ? c2x2 : (k == 1) ? -c1x2 : (k == 2) ? c1x2 : -c2x2;
-    } else {
-      w = cd * (r[V_U0 + A] + ua);
-      cd2 = cd + cd;
-    }
-    const T x2 = cd2 * r[V_U0 + A];             // 2 x D1(f u_A) weight
+    const T w = fma(cd, r[V_U0 + A], cdu);  // D1(f (u_A + u_A^c)) weight
+    const T x = cd * r[V_U0 + A];          // D1(f u_A) weight (times 2 p' below)
 #pragma unroll
     for (int i = 0; i < 3; ++i) t.rM[i] = mad(w, r[V_M0 + i], t.rM[i]);
-    t.rM[A] = mad(cd2, r[V_P], t.rM[A]);
-    t.rE = mad(w, r[V_E], mad(x2, r[V_P], t.rE));
+    t.rM[A] = mad(cd, r[V_P], t.rM[A]);
+    t.rE = mad(w, r[V_E], mad(x, r[V_P], t.rE));
     t.rrho = mad(cd, fma(ua, r[V_RHO], r[V_M0 + A]), t.rrho);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -785,8 +778,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           const T rinv = recip<T>(T(1) + rho_p);
           const T u0 = m0 * rinv, u1 = m1 * rinv, u2 = m2 * rinv;
           const T mu = mad(m2, u2, mad(m1, u1, m0 * u0));
-          const T p_p = c.gm1 * mad(T(-0.5), mu, E_p);    // Eq. 4: p - p_ref
-          const T T_p = mad(c.gM2, p_p, -rho_p) * rinv;  // Eq. 5: T - 1
+          const T p2 = c.gm1x2 * mad(T(-0.5), mu, E_p);  // Eq. 4: 2 (p - p_ref)
+          const T T_p = mad(c.hgM2, p2, -rho_p) * rinv;  // Eq. 5: T - 1
           rec[V_RHO] = rho_p;
           rec[V_M0] = m0;
           rec[V_M1] = m1;
@@ -795,7 +788,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           rec[V_U0] = u0;
           rec[V_U1] = u1;
           rec[V_U2] = u2;
-          rec[V_P] = p_p;
+          rec[V_P] = p2;
           rec[V_T] = T_p;
           store_rec(ring + ld_s[l] * NV, rec);
           if constexpr (ZT) {
@@ -835,8 +828,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
 #pragma unroll
     for (int j = 0; j < PP; ++j) oc[j] = (unsigned)zc * plane + own[j];
 
-    // accumulator of the centre points (fetched during phase 3, after the
-    // x0 terms, so that its latency overlaps the x1 and x2 terms)
+    // accumulator of the centre points (fetched as phase 3 starts, so that
+    // its latency overlaps the derivative terms)
     double accv[NF][PP];
     float dhi[NF][PP], dlo[NF][PP];  // double-float accumulator (DF mode)
     auto fetch_acc = [&]() {
@@ -899,6 +892,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     __syncthreads();
     // ---------------------------------------------------------------- phase 3
     {
+      fetch_acc();
       const int sy = ty + HALO, sx = tx + HALO;
       const T(*C)[SX][NV] = sm.ring[fc];
       T cen[NV];
@@ -930,7 +924,6 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[ty][sx + off[k]]; };
         axis_terms_any<0>(ld, sf, c, uc, t);
       }
-      fetch_acc();
       {
         const int off[4] = {-2, -1, 1, 2};
         auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy + off[k]][sx][0], r); };
@@ -972,22 +965,36 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         } else if constexpr (DF) {
           // binary32 stage, double-float accumulator (hi + lo, binary32
           // each): acc' = acc + (b dt R) by an error-free two-sum of hi and
-          // the increment, the error folded into lo and renormalised;
-          // Q_{k+1} = hi' + (lo' + (a - b) dt R).
+          // the increment, the error folded into lo; Q_{k+1} = hi' + (lo' +
+          // (a - b) dt R).  The pair (hi', lo') represents acc' whether or not
+          // it is normalised; the last stage of a step renormalises it, so
+          // that the state's hi fields are its binary32 rounding (the next
+          // step's stage-0 input), the others leave it as it is.
           const float bdt = a.b_dt32, ambdt = a.amb_dt32;
+          float hi3[NF], lo3[NF], rr[NF];
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            const float r = float(lane(R[f], j));
-            const float x = bdt * r;
+            rr[f] = float(lane(R[f], j));
+            const float x = bdt * rr[f];
             const float s = __fadd_rn(dhi[f][j], x);
             const float bb = __fsub_rn(s, dhi[f][j]);
             const float err = __fadd_rn(__fsub_rn(dhi[f][j], __fsub_rn(s, bb)), __fsub_rn(x, bb));
-            const float lo2 = __fadd_rn(dlo[f][j], err);
-            const float hi3 = __fadd_rn(s, lo2);
-            const float lo3 = __fsub_rn(lo2, __fsub_rn(hi3, s));
-            a.dacc_out[(long long)f * a.g.P + o] = hi3;
-            a.dacc_out[(long long)(NF + f) * a.g.P + o] = lo3;
-            qo[f] = TOUT(hi3 + fmaf(ambdt, r, lo3));
+            hi3[f] = s;
+            lo3[f] = __fadd_rn(dlo[f][j], err);
+          }
+          if (a.df_normalize) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const float h = __fadd_rn(hi3[f], lo3[f]);
+              lo3[f] = __fsub_rn(lo3[f], __fsub_rn(h, hi3[f]));
+              hi3[f] = h;
+            }
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            a.dacc_out[(long long)f * a.g.P + o] = hi3[f];
+            a.dacc_out[(long long)(NF + f) * a.g.P + o] = lo3[f];
+            qo[f] = TOUT(hi3[f] + fmaf(ambdt, rr[f], lo3[f]));
           }
         } else if constexpr (is_f64_class<T>()) {
           // binary64 (or double-float) stage: acc + b dt R and acc + a dt R,

@@ -28,6 +28,8 @@ struct Coef {
   T e0[3], e1[3], e2[3];
   T gm1;    // gamma - 1                    (Eq. 4)
   T gM2;    // gamma M^2                    (Eq. 5)
+  T gm1x2;  // 2 (gamma - 1): the fused kernels keep 2 p' (both uses of p in Eqs. 2-3 carry a factor 2)
+  T hgM2;   // gamma M^2 / 2: T' from 2 p'  (Eq. 5)
   T inv_re; // 1/Re (0 for Re = inf)        (Eqs. 2-3)
   T kappa;  // 1/((gamma-1) M^2 Pr Re)      (Eq. 3 heat flux)
   T H0;     // (rho E)_ref + p_ref = 1/((gamma-1) M^2): enthalpy of the reference state
@@ -73,6 +75,7 @@ struct StageArgs {
   // fields of binary32, P values each
   const float* dacc_in;
   float* dacc_out;
+  int df_normalize;  // double-float accumulator: renormalise (hi, lo) in this stage (the last of a step)
 };
 
 // Launch configuration chosen for one grid (the autotuner's output).
@@ -80,9 +83,7 @@ struct FusedConfig {
   int ty;  // in-plane tile height (tile is 32 x ty)
   int zc;  // planes per CTA
   int zq;  // binary32 paths: 0 = x2-neighbour records from the shared-memory
-           // ring, 1 = from a per-thread queue in tensor memory (TMEM),
-           // 2 = TMEM queue with two x2 planes per thread computed together
-           // in packed FP32x2 instructions (stages only; 32 x 8 tiles)
+           // ring, 1 = from a per-thread queue in tensor memory (TMEM)
   int px;  // binary32 paths: columns per thread (1, or 2 = columns x and x + 32
            // of a 64 x ty tile computed together)
 };
@@ -106,9 +107,6 @@ cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& c, con
 // the same two binary32 paths with the TMEM z queue (fused_fp32_tmem.cu)
 cudaError_t launch_fused_fp32_tmem(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                                    bool df, bool rhs_only, cudaStream_t s);
-// the two binary32 paths with two x2 planes per thread (fused_fp32_zpair.cu)
-cudaError_t launch_fused_fp32_zpair(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool df,
-                                    cudaStream_t s);
 int fused_num_ctas(const Geom& g, const FusedConfig& cfg);
 
 // Diagnostics and state conversion (diag.cu).

@@ -159,6 +159,7 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
   a.amb_dt = (RK_A[k] - RK_B[k]) * q.r.dt;
   a.b_dt32 = (float)a.b_dt;
   a.amb_dt32 = (float)a.amb_dt;
+  a.df_normalize = (k == 2);
   const int st = q.state;
   if (req_f64_registers(q.r.precision)) {
     double* S = r64(s, q, st);

@@ -281,10 +281,9 @@ def test_error_paths_fault_nothing(S):
     "precision,configs",
     [
         (1, [(8, 4, 0, 1), (8, 13, 0, 1), (16, 7, 0, 1), (16, 40, 0, 1), (8, 13, 1, 1), (16, 7, 1, 1),
-             (16, 40, 1, 1), (8, 4, 1, 1), (16, 4, 1, 1), (8, 4, 0, 2), (8, 13, 0, 2), (8, 40, 0, 2),
-             (8, 4, 2, 1), (8, 13, 2, 1), (8, 40, 2, 1)]),
+             (16, 40, 1, 1), (8, 4, 1, 1), (16, 4, 1, 1), (8, 4, 0, 2), (8, 13, 0, 2), (8, 40, 0, 2)]),
         (2, [(8, 4, 0, 1), (16, 7, 0, 1), (8, 13, 1, 1), (16, 40, 1, 1), (16, 5, 1, 1), (8, 5, 0, 2),
-             (8, 40, 0, 2), (8, 5, 2, 1), (8, 6, 2, 1), (8, 40, 2, 1)]),
+             (8, 40, 0, 2)]),
         (0, [(8, 4, 0, 1), (8, 9, 0, 1), (8, 40, 0, 1), (8, 4, 1, 1), (8, 13, 1, 1)]),
         (3, [(8, 4, 0, 1), (8, 40, 0, 1), (8, 5, 1, 1), (8, 40, 1, 1)]),
     ],
@@ -296,12 +295,10 @@ def test_launch_configs_are_bitwise_identical(S, precision, configs, n):
     full-record planes and two barriers per plane) change only the work
     decomposition and data movement: every point's arithmetic is the same, so the state (and
     the kinetic-energy history up to the order of its sums) is bitwise equal.
-    Two columns per thread, and two x2 planes per thread (z queue mode 2),
-    use packed two-lane instructions with their own multiply-add fusion:
-    each bitwise equal among its own configurations (odd planes per CTA leave
-    the last pair half empty), within the binary32 bar of the one-column
-    kernels.  Grids with x0 extents that are not multiples of 64 cover the
-    two-column tiles' ragged edge."""
+    Two columns per thread use packed two-lane instructions with their own
+    multiply-add fusion: bitwise equal among themselves, within the binary32
+    bar of the one-column kernels.  Grids with x0 extents that are not
+    multiples of 64 cover the two-column tiles' ragged edge."""
     dt = 1e-3
     q = to_dev(random_state(n, 23))
     ref = {}
@@ -313,17 +310,15 @@ def test_launch_configs_are_bitwise_identical(S, precision, configs, n):
         g.step_n(2, dt)
         hist = g.step_n_history(2, dt).cpu().numpy()
         out = g.get_state()
-        key = "planes" if zq == 2 else px
-        if key not in ref:
-            ref[key] = (out, hist)
+        if px not in ref:
+            ref[px] = (out, hist)
         else:
-            assert torch.equal(out, ref[key][0]), (ty, zc, zq, px)
-            assert np.allclose(hist, ref[key][1], rtol=1e-13, atol=0), (ty, zc, zq, px)
-    for key in (2, "planes"):
-        if key in ref:
-            errs = rel_fields(ref[key][0].cpu().numpy(), ref[1][0].cpu().numpy())
-            assert max(errs) <= 1e-5, (key, errs)
-            assert np.allclose(ref[key][1], ref[1][1], rtol=1e-6, atol=0), key
+            assert torch.equal(out, ref[px][0]), (ty, zc, zq, px)
+            assert np.allclose(hist, ref[px][1], rtol=1e-13, atol=0), (ty, zc, zq, px)
+    if 2 in ref:
+        errs = rel_fields(ref[2][0].cpu().numpy(), ref[1][0].cpu().numpy())
+        assert max(errs) <= 1e-5, errs
+        assert np.allclose(ref[2][1], ref[1][1], rtol=1e-6, atol=0)
 
 
 @pytest.mark.parametrize("precision", [1, 2])
@@ -345,44 +340,13 @@ def test_two_column_tiles_match_oracle(S, orc, precision, n):
     assert max(errs) <= 1e-5, errs
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("n,zc", [((64, 32, 24), 8), ((96, 20, 13), 13), ((40, 9, 7), 7), ((33, 17, 9), 4),
-                                  ((64, 64, 40), 40)])
-def test_two_plane_kernel_matches_oracle(S, orc, precision, n, zc):
-    """Two x2 planes per thread (z queue mode 2, packed two-lane binary32)
-    against the oracle, stage by stage and over 5 steps: ragged x0/x1 tiles,
-    odd plane counts per CTA (a half-empty last pair) and z chunks that wrap
-    the periodic edge."""
-    q = random_state(n, seed=73 + sum(n))
-    p = orc.params(n)
-    dt = 1e-3
-    g = S.Grid(n, precision, S.SBLI_FUSED)
-    g.set_config(8, zc, 2, 1)
-    g.set_state(to_dev(q))
-    acc = q.copy()
-    qk = q
-    for k in range(2):
-        g.rk_stage(k, dt)
-        q_next, acc = orc.stage(p, k, dt, qk, acc)
-        gq, ga = g.get_stage()
-        assert max(rel_fields(gq.cpu().numpy(), q_next)) <= 1e-5, (k, "stage field")
-        assert max(rel_fields(ga.cpu().numpy(), acc)) <= 1e-5, (k, "accumulator")
-        qk = q_next
-    g.rk_stage(2, dt)
-    want1 = orc.step(p, q, dt, 1)
-    assert max(rel_fields(g.get_state().cpu().numpy(), want1)) <= 1e-5
-    g.step_n(4, dt)
-    errs = rel_fields(g.get_state().cpu().numpy(), orc.step(p, want1, dt, 4))
-    assert max(errs) <= 1e-5, errs
-
-
 def test_autotune_keeps_state_and_picks_a_valid_config(S):
     n = (64, 64, 64)
     g = S.Grid(n, S.SBLI_FP32, S.SBLI_FUSED)
     g.init_tgv()
     before = g.get_state()
     ty, zc, zq, px, ms = g.autotune(reps=2)
-    assert ty in (8, 16) and 4 <= zc <= n[2] and zq in (0, 1, 2) and px in (1, 2) and ms > 0
+    assert ty in (8, 16) and 4 <= zc <= n[2] and zq in (0, 1) and px in (1, 2) and ms > 0
     assert torch.equal(g.get_state(), before)
     assert g.config() == (ty, zc, zq, px)
     g.step_n(1, 1e-3)
@@ -391,14 +355,8 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
     with pytest.raises(S.SbliError):
         g.set_config(12, 8, 1)
     with pytest.raises(S.SbliError):
-        g.set_config(8, 8, 3)
-    with pytest.raises(S.SbliError):
-        g.set_config(16, 8, 2)  # two planes per thread: 32 x 8 tiles
-    with pytest.raises(S.SbliError):
-        g.set_config(8, 8, 2, 2)  # ... and one column per thread
+        g.set_config(8, 8, 2)
     d = S.Grid(n, S.SBLI_FP64, S.SBLI_FUSED)
-    with pytest.raises(S.SbliError):
-        d.set_config(8, 8, 2)  # two planes per thread: binary32 stage fields only
     d.set_config(8, 8, 1)  # binary64 records in the TMEM queue
     with pytest.raises(S.SbliError):
         d.set_config(4, 8, 1)  # binary64 tiles are 32 x 8

@@ -48,8 +48,6 @@ CONCURRENT = [
     ((80, 48, 56), 2, (8, 12, 1, 1)),
     ((64, 64, 32), 0, None),
     ((48, 40, 36), 3, None),
-    ((72, 48, 44), 2, (8, 11, 2, 1)),
-    ((64, 40, 30), 1, (8, 30, 2, 1)),
 ]
 
 
