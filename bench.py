@@ -110,8 +110,10 @@ def parse():
     ap.add_argument("--df64-leg-steps", type=int, default=40)
     ap.add_argument("--ens-steps", type=int, default=40)
     ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-nmax", type=int, default=128)
-    ap.add_argument("--serve-steps-hi", type=int, default=300)
+    ap.add_argument("--serve-requests-low", type=int, default=10)
+    ap.add_argument("--serve-rate-low", type=float, default=1.0)
+    ap.add_argument("--serve-nmax", type=int, default=256)
+    ap.add_argument("--serve-steps-hi", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-planes", type=int, default=8,
                     help="the oracle's bounded sample: a periodic n x n x planes slab of the workload's planes")
@@ -394,11 +396,12 @@ def energy_per_pt_stage(g, stream, points, stage_ms, dt, nvml, seconds=1.0):
             "source": "nvmlDeviceGetTotalEnergyConsumption delta over further steps after the timed ones"}
 
 
-def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None, precision=None):
+def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None, precision=None, tune=True):
     """64 Taylor-Green members, N uniform over {32,48,64,96,128}, Re ~ U[100,1600],
     M ~ U[0.1,0.4], amplitude ~ U(0.9,1.1); binary32 stages with a binary64
     accumulator (or, precision SBLI_FP32_DF, a double-float one); one
-    persistent launch per stage, graph-captured steps."""
+    persistent launch per stage, graph-captured steps, schedule (z-queue mode,
+    planes per work item per size class) picked by the batch autotuner."""
     import torch
 
     from paper_1709_09713_gb300 import workloads
@@ -410,6 +413,13 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None, preci
                 stream=stream)
     with torch.cuda.stream(stream):
         b.init_tgv([m.amplitude for m in members])
+    default_items = b.work_items()
+    zq, tuned_ms = b.autotune(3) if tune else (b.schedule()[0], None)
+    zq, zc = b.schedule()
+    by_n = {}
+    for m, z in zip(members, zc):
+        by_n.setdefault(str(m.n), z)
+    with torch.cuda.stream(stream):
         b.step_n(max(warmup, 6), dt)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -432,6 +442,8 @@ def ensemble_leg(S, steps, warmup, dt, ws, count=64, seed=1709, nvml=None, preci
                         f"fp32 + {acc}, persistent launch per stage", "value": 3.0 * pts * steps * ws / (ms / 1e3),
             "unit": "pt-stage/s", "steps": steps, "points": pts, "work_items_per_stage": items,
             "stage_ms": ms / (3 * steps), "launches_per_stage": 1, "energy": energy,
+            "schedule": {"autotuned": bool(tune), "z_queue": zq, "planes_per_item_by_n": by_n,
+                         "work_items_default_schedule": default_items, "tuned_stage0_ms": tuned_ms},
             "hbm": {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                     "peak_source": kind, "bytes_per_pt_stage": ALG_BYTES["fp32"]}}
 
@@ -475,14 +487,20 @@ def serving_leg(S, count, rate_hz, nmin, nmax, steps_lo, steps_hi, seed=20, aren
     lat = sorted(done_t - arrival[rid] for rid, (r, done_t) in res.items())
     work = sum(3.0 * r.points * r.steps for r, _ in res.values())
 
-    def pct(p):
-        return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+    def pct(v, p):
+        return v[min(len(v) - 1, int(round(p / 100.0 * (len(v) - 1))))] if v else None
+
+    def lane_lat(f64_lane):
+        v = sorted(done_t - arrival[rid] for rid, (r, done_t) in res.items()
+                   if (r.precision in (S.SBLI_FP64, S.SBLI_DF64)) == f64_lane)
+        return {"requests": len(v), "p50_latency_s": pct(v, 50), "p99_latency_s": pct(v, 99)}
 
     f64 = "fp64" if fp64_as == S.SBLI_FP64 else "fp64 (double-float arithmetic)"
     return {"workload": f"serving: {count} Poisson requests at {rate_hz} req/s, N log-uniform [{nmin},{nmax}], "
                         f"steps U{{{steps_lo}..{steps_hi}}}, {f64}/fp32 50/50, dt 1e-3",
             "value": work / wall, "unit": "pt-stage/s", "requests": count, "wall_s": wall,
-            "p50_latency_s": pct(50), "p99_latency_s": pct(99), "max_latency_s": lat[-1],
+            "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99), "max_latency_s": lat[-1],
+            "by_lane": {"fp64_lane": lane_lat(True), "fp32_lane": lane_lat(False)},
             "offered_pt_stage_per_s": sum(3.0 * q.n**3 * q.steps for q in trace) / max(trace[-1].arrival_s, 1e-9)}
 
 
@@ -710,12 +728,13 @@ def run_ours(args):
                         algorithms_leg(S, 256, args.alg_steps, 1, 1e-3, ws, nvml),
                         ensemble_leg(S, args.ens_steps, 6, 1e-3, ws, nvml=nvml),
                         ensemble_leg(S, args.ens_steps, 6, 1e-3, ws, nvml=nvml, precision=S.SBLI_FP32_DF),
+                        # the serving distribution: N log-uniform [32,256], steps U{50..2000}, FP64/FP32 50/50
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi),
                         serving_leg(S, args.serve_requests, 20.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
                                     fp64_as=S.SBLI_DF64),
                         # below saturation: latency close to each request's own service time
-                        serving_leg(S, args.serve_requests, 5.0, 32, args.serve_nmax, 50, args.serve_steps_hi,
-                                    fp64_as=S.SBLI_DF64)]
+                        serving_leg(S, args.serve_requests_low, args.serve_rate_low, 32, args.serve_nmax, 50,
+                                    args.serve_steps_hi, fp64_as=S.SBLI_DF64)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, args.cpu_sample_planes, args.cpu_sample_steps)
     if rank == 0:

@@ -238,7 +238,8 @@ SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_
  * Batched ensembles: up to 64 members (each its own grid size, Re, M, Pr,
  * gamma, L) advanced together.  Every Runge-Kutta stage of all members is one
  * persistent kernel launch that walks the members' work items (z chunk x
- * 32 x 8 tile); step loops are captured as CUDA graphs.  Any precision of
+ * 32 x 8 tile, the z chunk per member set by the schedule below); step loops
+ * are captured as CUDA graphs.  Any precision of
  * sbli_precision, as for single grids (others: SBLI_EINVAL).  Members'
  * results are bitwise those of the same member run alone as a single grid
  * with tile height 8.
@@ -253,6 +254,26 @@ SBLI_API int sbli_batch_destroy(sbli_batch* b);
 SBLI_API int sbli_batch_count(const sbli_batch* b, int* count);
 /* Total work items of one stage (for scheduling diagnostics). */
 SBLI_API int sbli_batch_work_items(const sbli_batch* b, long long* items);
+/* The batch's schedule: z_queue (0 = x2-neighbour records from the
+ * shared-memory ring, 1 = from the per-thread TMEM queue, as for single grids)
+ * and each member's planes per work item (planes_per_item[count]: the z chunk
+ * a CTA marches through; >= 4, clamped to the member's n2).  A batch starts
+ * with the TMEM queue for binary32 precisions and the ring otherwise, and
+ * min(n2, 32) planes per item.  Every schedule gives bitwise the same
+ * results.  set_schedule (between steps; SBLI_EINVAL for z_queue outside 0..1
+ * or fewer than 4 planes) drops the captured step graphs; planes_per_item may
+ * be NULL in both calls (keep, or do not return, the per-member values). */
+SBLI_API int sbli_batch_get_schedule(const sbli_batch* b, int* z_queue, int* planes_per_item);
+SBLI_API int sbli_batch_set_schedule(sbli_batch* b, int z_queue, const int* planes_per_item);
+/* Autotuner of the schedule: times non-destructive stage-0 launches (reps
+ * each; they read the state and write only the accumulator and stage
+ * registers) of every z_queue mode with one planes-per-item value for all
+ * members (8, 16, 32, 64, 128, whole member), then refines the planes per
+ * item of each size class (members with the same n2) in turn, and keeps the
+ * fastest schedule.  The state is not changed.  Synchronises the batch's
+ * stream.  *z_queue and *best_stage_ms (may be NULL) return the choice and
+ * its stage time; sbli_batch_get_schedule returns the planes per item. */
+SBLI_API int sbli_batch_autotune(sbli_batch* b, int reps, int* z_queue, float* best_stage_ms);
 /* Taylor-Green initial field per member with amplitudes[count]. */
 SBLI_API int sbli_batch_init_tgv(sbli_batch* b, const double* amplitudes);
 /* Member state in/out as plain binary64 conserved variables (as sbli_set_state). */
@@ -272,13 +293,16 @@ SBLI_API int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstro
  * order and are admitted when one of max_slots slots and a block of the
  * caller's device arena are free (first fit; with backfill != 0 a later
  * request that fits may pass one that does not).  Admitted requests keep
- * their state resident; each sbli_server_tick advances every active request
- * by one time step (the requests of each precision as one persistent
- * multi-member launch per stage; binary64-register precisions on the first
- * stream, binary32 ones on the second, which overlap on the device), then
- * retires the finished ones: binary64 kinetic energy and
- * enstrophy of the final state, optional copy of the state to `result`, and
- * release of the block.  A request's result equals the same problem run
+ * their state resident and run in two independent lanes: binary64-register
+ * precisions on the first stream, binary32 ones on the second, which overlap
+ * on the device and never wait for each other.  A lane advances all its
+ * requests together in batches of K time steps (the requests of each
+ * precision as one persistent multi-member launch per stage), K sized for a
+ * few milliseconds of device time and never past the smallest remaining step
+ * count of the batch.  When a lane's batch has completed, its finished
+ * requests are retired (binary64 kinetic energy and enstrophy of the final
+ * state, optional copy of the state to `result`, release of the block) and
+ * its next batch starts.  A request's result equals the same problem run
  * alone as a single grid with tile height 8, bitwise.
  * --------------------------------------------------------------------- */
 typedef struct sbli_server sbli_server;
@@ -318,8 +342,11 @@ SBLI_API int sbli_server_destroy(sbli_server* s);
 SBLI_API int sbli_server_request_bytes(const sbli_request* r, size_t* bytes);
 /* Queue a request (copied); SBLI_ENOMEM if it can never fit the arena. */
 SBLI_API int sbli_server_submit(sbli_server* s, const sbli_request* r, long long* id);
-/* Admit, advance every active request one step, retire finished ones.
- * Synchronises both streams; *completed = requests retired by this tick. */
+/* Admit waiting requests, then for each lane whose batch has completed:
+ * retire its finished requests and launch its next batch (a lane still
+ * running is left alone).  If neither lane could make progress, waits up to
+ * about 2 ms for one to finish.  Returns without synchronising a running
+ * lane; *completed = requests retired by this tick. */
 SBLI_API int sbli_server_tick(sbli_server* s, int* completed);
 /* Move up to max retired requests' results into out; *n = how many. */
 SBLI_API int sbli_server_poll(sbli_server* s, sbli_result* out, int max, int* n);

@@ -74,52 +74,44 @@ __global__ void __launch_bounds__(256) batch_ke_finalize(const double* __restric
 }
 
 // ---- launchers (declared in batch_kernel.cuh)
-// binary32 members: TMEM z queue and 3-slot ring, 3 CTAs per SM (the grid is
-// sized for that by the caller: batch_ctas_per_sm)
+// Launch one instantiation, setting its shared-memory limit on first use.
+template <typename T, typename TIN, typename TOUT, bool WITH_KE, bool ZT, bool DF>
+static cudaError_t launch_batch_k(const BatchParams<T>& p, int grid, cudaStream_t s) {
+  auto k = batch_stage_kernel<T, TIN, TOUT, 8, WITH_KE, ZT, DF>;
+  const size_t smem = sizeof(FusedSmem<T, 8, ZT>);
+  static std::atomic<unsigned long long> done{0};
+  if (cudaError_t e = ensure_smem_limit(k, smem, done)) return e;
+  k<<<grid, TX * 8, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TIN, typename TOUT, bool DF>
+static cudaError_t launch_batch_zq(const BatchParams<T>& p, int grid, cudaStream_t s, int zq) {
+  if (zq)
+    return p.ke_items ? launch_batch_k<T, TIN, TOUT, true, true, DF>(p, grid, s)
+                      : launch_batch_k<T, TIN, TOUT, false, true, DF>(p, grid, s);
+  return p.ke_items ? launch_batch_k<T, TIN, TOUT, true, false, DF>(p, grid, s)
+                    : launch_batch_k<T, TIN, TOUT, false, false, DF>(p, grid, s);
+}
+
+// binary32 members (every stage input is binary32; the grid is sized by the
+// caller with batch_ctas_per_sm for the z-queue mode)
 template <>
-cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s, bool df) {
-  const size_t smem = sizeof(FusedSmem<float, 8, true>);
-  if (df) {  // double-float accumulator: every stage input is binary32
-    static std::atomic<unsigned long long> f0{0}, f1{0};
-    if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, false, true, true>, smem, f0))
-      return e;
-    if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, true, true, true>, smem, f1))
-      return e;
-    if (p.ke_items) batch_stage_kernel<float, float, float, 8, true, true, true><<<grid, TX * 8, smem, s>>>(p);
-    else batch_stage_kernel<float, float, float, 8, false, true, true><<<grid, TX * 8, smem, s>>>(p);
-    return cudaGetLastError();
-  }
+cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int grid, cudaStream_t s, bool df, int zq) {
   if (in64) return cudaErrorInvalidValue;  // stages read the binary32 copy of the state
-  static std::atomic<unsigned long long> d0{0}, d1{0};
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, false, true>, smem, d0)) return e;
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<float, float, float, 8, true, true>, smem, d1)) return e;
-  if (p.ke_items) batch_stage_kernel<float, float, float, 8, true, true><<<grid, TX * 8, smem, s>>>(p);
-  else batch_stage_kernel<float, float, float, 8, false, true><<<grid, TX * 8, smem, s>>>(p);
-  return cudaGetLastError();
+  if (df) return launch_batch_zq<float, float, float, true>(p, grid, s, zq);
+  return launch_batch_zq<float, float, float, false>(p, grid, s, zq);
 }
 
 template <>
-cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s, bool) {
-  const size_t smem = sizeof(FusedSmem<dfloat, 8>);
-  static std::atomic<unsigned long long> d0{0}, d1{0};
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<dfloat, double, double, 8, false>, smem, d0)) return e;
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<dfloat, double, double, 8, true>, smem, d1)) return e;
-  if (p.ke_items) batch_stage_kernel<dfloat, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
-  else batch_stage_kernel<dfloat, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
-  return cudaGetLastError();
+cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s, bool, int zq) {
+  return launch_batch_zq<dfloat, double, double, false>(p, grid, s, zq);
 }
 
 template <>
-cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s, bool) {
-  const size_t smem = sizeof(FusedSmem<double, 8>);
-  static std::atomic<unsigned long long> d0{0}, d1{0};
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<double, double, double, 8, false>, smem, d0)) return e;
-  if (cudaError_t e = ensure_smem_limit(batch_stage_kernel<double, double, double, 8, true>, smem, d1)) return e;
-  if (p.ke_items) batch_stage_kernel<double, double, double, 8, true><<<grid, TX * 8, smem, s>>>(p);
-  else batch_stage_kernel<double, double, double, 8, false><<<grid, TX * 8, smem, s>>>(p);
-  return cudaGetLastError();
+cudaError_t launch_batch_t<double>(const BatchParams<double>& p, bool, int grid, cudaStream_t s, bool, int zq) {
+  return launch_batch_zq<double, double, double, false>(p, grid, s, zq);
 }
-
 
 cudaError_t launch_batch_ke_finalize(const double* items, const long long* begin, const double* inv_p, double* out,
                                      int count, cudaStream_t s) {
@@ -157,6 +149,7 @@ size_t balign(size_t v) { return (v + BALIGN - 1) / BALIGN * BALIGN; }
 
 struct MemberLayout {
   int n[3];
+  int zc;  // planes per work item (the schedule; batch_zc at creation)
   long long P;
   size_t off64, off32;  // byte offsets inside the binary64 / binary32 register regions
 };
@@ -183,17 +176,20 @@ BatchLayout batch_layout(int count, const int* n, int precision) {
     MemberLayout& M = L.m[i];
     for (int a = 0; a < 3; ++a) M.n[a] = n[3 * i + a];
     M.P = (long long)M.n[0] * M.n[1] * M.n[2];
+    M.zc = batch_zc(M.n[2]);
     M.off64 = o64;
     M.off32 = o32;
     o64 += balign((size_t)M.P * 5 * sizeof(double));
     o32 += balign((size_t)M.P * 5 * sizeof(float));
-    L.total_items += member_items(M.n);
+    L.total_items += member_items(M.n, std::min(4, M.n[2]));  // the most items any schedule gives
   }
   L.reg64 = o64;
   L.reg32 = batch_f64_registers(precision) ? 0 : o32;
   L.n64 = batch_f64_registers(precision) ? 3 : 2;
   L.n32 = batch_f64_registers(precision) ? 0 : 2;
   L.items_bytes = balign((size_t)(2 * L.total_items + 2) * sizeof(double));
+  L.total_items = 0;
+  for (const MemberLayout& M : L.m) L.total_items += member_items(M.n, M.zc);
   // per member: KE result pair, 1/P, item begin; plus the KE kernel partials
   L.misc_bytes = balign((size_t)count * 2 * sizeof(double)) + balign((size_t)count * sizeof(double)) +
                  balign((size_t)(count + 1) * sizeof(long long)) + balign(2 * 1024 * sizeof(double));
@@ -217,6 +213,7 @@ struct sbli_batch {
   double* ke_scratch; // partials of the single-member KE kernel
   int state;
   long long steps_done;
+  int zq;             // z-queue mode of the batch kernel (the schedule)
   int grid_ctas;      // persistent grid size
   // one graph of GRAPH_STEPS steps per starting rotation
   static constexpr int GRAPH_STEPS = 6;
@@ -235,7 +232,7 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
   const MemberLayout& M = b->L.m[m];
   StageArgs a{};
   a.g = member_geom(M);
-  a.zc = batch_zc(M.n[2]);
+  a.zc = M.zc;
   a.a_dt = RK_A[k] * dt;
   a.b_dt = RK_B[k] * dt;
   a.amb_dt = (RK_A[k] - RK_B[k]) * dt;
@@ -288,13 +285,13 @@ cudaError_t enqueue_batch_stage_t(sbli_batch* b, int k, int state, double dt, do
     p.item_begin[m] = acc;
     p.tiles_x[m] = (M.n[0] + TX - 1) / TX;
     p.tiles_y[m] = (M.n[1] + 7) / 8;
-    acc += member_items(M.n);
+    acc += member_items(M.n, M.zc);
     p.a[m] = member_stage(b, m, k, state, dt, &in64);
     p.c[m] = make_coef<T>(M.n, b->params[m]);
   }
   p.item_begin[b->count] = acc;
   p.total_items = acc;
-  return launch_batch_t<T>(p, in64, b->grid_ctas, s, b->precision == SBLI_FP32_DF);
+  return launch_batch_t<T>(p, in64, b->grid_ctas, s, b->precision == SBLI_FP32_DF, b->zq);
 }
 
 cudaError_t enqueue_batch_stage(sbli_batch* b, int k, int state, double dt, double* ke_items, cudaStream_t s) {
@@ -337,6 +334,35 @@ int batch_build_graph(sbli_batch* b, int state, double dt) {
   b->graph[state] = exec;
   b->graph_dt[state] = dt;
   return SBLI_OK;
+}
+
+// Item ranges of the members under the current schedule, for the KE
+// finalisation (device copy, written on the batch's stream).
+cudaError_t upload_item_begin(sbli_batch* b) {
+  std::vector<long long> beg(b->count + 1);
+  long long acc = 0;
+  for (int m = 0; m < b->count; ++m) {
+    beg[m] = acc;
+    acc += member_items(b->L.m[m].n, b->L.m[m].zc);
+  }
+  beg[b->count] = acc;
+  b->L.total_items = acc;
+  cudaError_t e = cudaMemcpyAsync(b->begin, beg.data(), (b->count + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // beg is a host temporary
+  return e;
+}
+
+// Apply a schedule (z-queue mode, planes per item of each member); the
+// captured step graphs are rebuilt on the next step.
+cudaError_t apply_schedule(sbli_batch* b, int zq, const std::vector<int>& zc) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->zq = zq;
+  b->grid_ctas = sms * batch_ctas_per_sm(b->precision, zq);
+  for (int m = 0; m < b->count; ++m) b->L.m[m].zc = zc[m];
+  batch_drop_graphs(b);
+  return upload_item_begin(b);
 }
 
 int check_batch(const sbli_batch* b, int member) {
@@ -407,21 +433,14 @@ int sbli_batch_create(sbli_batch** out, int count, const int* n, const sbli_para
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->grid_ctas = sms * batch_ctas_per_sm(precision);
+  b->zq = batch_default_zq(precision);
+  b->grid_ctas = sms * batch_ctas_per_sm(precision, b->zq);
   // per-member constants for the KE finalisation
   std::vector<double> inv(count);
-  std::vector<long long> beg(count + 1);
-  long long acc = 0;
-  for (int m = 0; m < count; ++m) {
-    inv[m] = 1.0 / (double)b->L.m[m].P;
-    beg[m] = acc;
-    acc += member_items(b->L.m[m].n);
-  }
-  beg[count] = acc;
+  for (int m = 0; m < count; ++m) inv[m] = 1.0 / (double)b->L.m[m].P;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->inv_p, inv.data(), count * sizeof(double), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->begin, beg.data(), (count + 1) * sizeof(long long), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = upload_item_begin(b);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     delete b;
@@ -580,6 +599,97 @@ int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstrophy) {
 int sbli_batch_work_items(const sbli_batch* b, long long* items) {
   if (!b || !items) return bfail(SBLI_EINVAL, "null argument");
   *items = b->L.total_items;
+  return SBLI_OK;
+}
+
+int sbli_batch_get_schedule(const sbli_batch* b, int* z_queue, int* planes_per_item) {
+  if (!b || !z_queue) return bfail(SBLI_EINVAL, "null argument");
+  *z_queue = b->zq;
+  if (planes_per_item)
+    for (int m = 0; m < b->count; ++m) planes_per_item[m] = b->L.m[m].zc;
+  return SBLI_OK;
+}
+
+int sbli_batch_set_schedule(sbli_batch* b, int z_queue, const int* planes_per_item) {
+  if (int rc = check_batch(b, 0)) return rc;
+  if (z_queue < 0 || z_queue > 1) return bfail(SBLI_EINVAL, "z_queue %d not 0 or 1", z_queue);
+  std::vector<int> zc(b->count);
+  for (int m = 0; m < b->count; ++m) {
+    zc[m] = planes_per_item ? planes_per_item[m] : b->L.m[m].zc;
+    if (zc[m] < 4) return bfail(SBLI_EINVAL, "member %d: planes per item %d < 4", m, zc[m]);
+    zc[m] = std::min(zc[m], b->L.m[m].n[2]);
+  }
+  SBLI_BTRY(apply_schedule(b, z_queue, zc), "schedule");
+  return SBLI_OK;
+}
+
+int sbli_batch_autotune(sbli_batch* b, int reps, int* z_queue, float* best_stage_ms) {
+  if (int rc = check_batch(b, 0)) return rc;
+  if (reps < 1) return bfail(SBLI_EINVAL, "reps must be >= 1");
+  cudaEvent_t e0, e1;
+  SBLI_BTRY(cudaEventCreate(&e0), "cudaEventCreate");
+  if (cudaError_t ce = cudaEventCreate(&e1)) {
+    cudaEventDestroy(e0);
+    return bcuda(ce, "cudaEventCreate");
+  }
+  // time one schedule: one untimed and `reps` timed stage-0 launches, which
+  // read the state and write only the accumulator and stage registers
+  cudaError_t err = cudaSuccess;
+  auto time_schedule = [&](int zq, const std::vector<int>& zc) -> float {
+    if (err == cudaSuccess) err = apply_schedule(b, zq, zc);
+    if (err == cudaSuccess) err = enqueue_batch_stage(b, 0, b->state, 1e-6, nullptr, b->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = enqueue_batch_stage(b, 0, b->state, 1e-6, nullptr, b->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 1e30f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    return err == cudaSuccess ? ms / (float)reps : 1e30f;
+  };
+  auto uniform = [&](int Z) {
+    std::vector<int> zc(b->count);
+    for (int m = 0; m < b->count; ++m) zc[m] = std::max(4, std::min(Z, b->L.m[m].n[2]));
+    return zc;
+  };
+  const int Zs[6] = {8, 16, 32, 64, 128, 1 << 24};
+  // 1. one z-queue mode and one planes-per-item value for every member
+  int best_zq = b->zq;
+  std::vector<int> best_zc(b->count);
+  for (int m = 0; m < b->count; ++m) best_zc[m] = b->L.m[m].zc;
+  float best = time_schedule(best_zq, best_zc);
+  for (int zq = 0; zq <= 1; ++zq)
+    for (int Z : Zs) {
+      const std::vector<int> zc = uniform(Z);
+      const float ms = time_schedule(zq, zc);
+      if (ms < best) {
+        best = ms;
+        best_zq = zq;
+        best_zc = zc;
+      }
+    }
+  // 2. each size class (members with the same x2 extent) refined in turn
+  std::vector<int> classes;
+  for (int m = 0; m < b->count; ++m)
+    if (std::find(classes.begin(), classes.end(), b->L.m[m].n[2]) == classes.end()) classes.push_back(b->L.m[m].n[2]);
+  for (int n2 : classes) {
+    for (int Z : Zs) {
+      std::vector<int> zc = best_zc;
+      for (int m = 0; m < b->count; ++m)
+        if (b->L.m[m].n[2] == n2) zc[m] = std::max(4, std::min(Z, n2));
+      if (zc == best_zc) continue;
+      const float ms = time_schedule(best_zq, zc);
+      if (ms < best) {
+        best = ms;
+        best_zc = zc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return bcuda(err, "autotune launch");
+  SBLI_BTRY(apply_schedule(b, best_zq, best_zc), "schedule");
+  if (z_queue) *z_queue = best_zq;
+  if (best_stage_ms) *best_stage_ms = best;
   return SBLI_OK;
 }
 

@@ -116,10 +116,10 @@ cudaError_t launch_widen(long long n, const float* src, double* dst, cudaStream_
 }
 
 // The binary32 copy of a binary64 state that stage 0 of the binary32 path
-// reads: the same narrowing the stage kernels apply (narrow_f64_fast).
+// reads: the same narrowing the stage kernels apply (narrow_f64_rna).
 __global__ void narrow_kernel(long long n, const double* __restrict__ src, float* __restrict__ dst) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    dst[i] = narrow_f64_fast(src[i]);
+    dst[i] = narrow_f64_rna(src[i]);
 }
 
 cudaError_t launch_narrow(long long n, const double* src, float* dst, cudaStream_t s) {

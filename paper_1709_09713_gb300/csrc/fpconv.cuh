@@ -72,4 +72,27 @@ __device__ __forceinline__ float narrow_f64_fast(double d) {
   return __uint_as_float(bits);
 }
 
+// The narrowing of the binary32 stage values and of the binary32 copy of
+// the state (binary32 stages with a binary64 accumulator): round to nearest,
+// ties away from zero (the same error bound as ties-to-even, half a unit in
+// the last place).  One funnel shift brings the 23 kept mantissa bits and the
+// low 9 exponent bits together; adding 0x40000000 rebases the exponent
+// (e - 896, taken modulo 2^9, lands in bits 30..23 with bit 31 clear for
+// every binary32-normal result); the first dropped bit is the rounding
+// increment, whose carry moves into the exponent when the mantissa
+// overflows.  Results below the binary32 normal range are signed zero;
+// magnitudes of 2^128 and above, infinities and NaNs give signed infinity (a
+// NaN stays NaN in the binary64 accumulator and state).
+__device__ __forceinline__ float narrow_f64_rna(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d);
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned t = __funnelshift_l(lo, hi, 3) + 0x40000000u + ((lo >> 28) & 1u);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned eb = (hi >> 20) & 0x7FFu;
+  unsigned bits = t | sign;
+  bits = (eb < 897u) ? sign : bits;
+  bits = (eb > 1150u) ? (sign | 0x7F800000u) : bits;
+  return __uint_as_float(bits);
+}
+
 }  // namespace sbli

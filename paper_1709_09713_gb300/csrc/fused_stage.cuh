@@ -1008,14 +1008,15 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         } else {
           // binary32 stage, binary64 accumulator: one DADD per field,
           //   acc' = acc + (b dt R),  Q_{k+1} = float(acc') + (a - b) dt R
-          // (conversions by integer re-packing, fpconv.cuh)
+          // (conversions by integer re-packing, fpconv.cuh; the narrowing
+          // rounds to nearest, ties away from zero)
           const float bdt = a.b_dt32, ambdt = a.amb_dt32;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const float r = float(lane(R[f], j));
             const double accn = accv[f][j] + widen_f32_fast(bdt * r);
             a.acc_out[(long long)f * a.g.P + o] = accn;
-            qo[f] = TOUT(narrow_f64_fast(accn) + ambdt * r);
+            qo[f] = TOUT(narrow_f64_rna(accn) + ambdt * r);
           }
         }
         if constexpr (!RHS_ONLY) {

@@ -4,14 +4,19 @@
 // in a FIFO and are admitted when a slot and a block of the caller's device
 // arena are free (first-fit allocation with coalescing of freed blocks).  An
 // admitted request's state stays resident in its block for its whole life.
-// Every tick advances all active requests by one time step: for each stage,
-// the requests of each precision form one persistent multi-member launch
-// (batch_kernel.cuh); the binary64-register groups (binary64, double-float
-// arithmetic) run on one stream and the binary32 groups (either accumulator)
-// on another, so their work overlaps on the device.  Finished requests are retired at the
-// end of the tick (binary64 kinetic energy and enstrophy, optional copy of the
-// final state to a caller buffer) and their memory is released, which lets
-// waiting requests in on the next tick.
+// The requests run in two independent lanes: the binary64-register
+// precisions (binary64, double-float arithmetic) on one stream, the binary32
+// ones (either accumulator) on another, so their work overlaps on the device
+// and neither waits for the other.  A lane advances its requests in batches
+// of K time steps (each stage of each precision one persistent multi-member
+// launch, batch_kernel.cuh), K chosen so that a batch takes about
+// LANE_BATCH_MS of device time (measured with events on the lane's stream)
+// and no request of the batch overshoots its step count.  A tick looks at
+// each lane: if its batch has completed, the lane's finished requests are
+// retired (binary64 kinetic energy and enstrophy, optional copy of the final
+// state to a caller buffer, release of their memory) and the next batch is
+// launched; a lane still running is left alone.  Waiting requests are
+// admitted at the start of every tick and join their lane's next batch.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -21,6 +26,7 @@
 #include <chrono>
 #include <deque>
 #include <map>
+#include <thread>
 #include <vector>
 
 #include "batch_kernel.cuh"
@@ -122,6 +128,20 @@ size_t request_bytes(const sbli_request& r, size_t* reg64, size_t* reg32) {
 
 }  // namespace
 
+// Device time one lane batch aims at: long enough to amortise the host's
+// launch work over several steps, short enough that a request arriving
+// meanwhile waits only a few milliseconds to join.
+constexpr double LANE_BATCH_MS = 4.0;
+constexpr int LANE_MAX_STEPS = 256;
+
+struct Lane {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // start and end of the batch in flight
+  bool busy = false;
+  int steps = 0;            // time steps of the batch in flight
+  double ms_per_step = 0;   // running estimate (0: none yet)
+};
+
 struct sbli_server {
   char* arena;
   size_t arena_bytes;
@@ -137,6 +157,7 @@ struct sbli_server {
   long long next_id = 0;
   long long ticks = 0;
   int grid64, grid32;
+  Lane lane[2];  // 0: binary64-register precisions on s64; 1: binary32 precisions on s32
   std::chrono::steady_clock::time_point t0;
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
@@ -192,13 +213,14 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
   return a;
 }
 
-// Stage k of every active request of one precision, in launches of at most
-// BATCH_MAX_MEMBERS members.
+// Stage k of the requests of `run` that have the given precision, in
+// launches of at most BATCH_MAX_MEMBERS members.
 template <typename T>
-cudaError_t launch_group(sbli_server* s, int k, int precision, cudaStream_t st, int grid) {
+cudaError_t launch_group(sbli_server* s, int k, int precision, const std::vector<Req*>& run, cudaStream_t st,
+                         int grid) {
   std::vector<const Req*> mem;
-  for (const Req& q : s->active)
-    if (q.r.precision == precision) mem.push_back(&q);
+  for (const Req* q : run)
+    if (q->r.precision == precision) mem.push_back(q);
   for (size_t base = 0; base < mem.size(); base += BATCH_MAX_MEMBERS) {
     const int cnt = (int)std::min<size_t>(BATCH_MAX_MEMBERS, mem.size() - base);
     BatchParams<T> p;
@@ -218,7 +240,7 @@ cudaError_t launch_group(sbli_server* s, int k, int precision, cudaStream_t st, 
     }
     p.item_begin[cnt] = acc;
     p.total_items = acc;
-    cudaError_t e = launch_batch_t<T>(p, in64, grid, st, precision == SBLI_FP32_DF);
+    cudaError_t e = launch_batch_t<T>(p, in64, grid, st, precision == SBLI_FP32_DF, batch_default_zq(precision));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -239,9 +261,11 @@ int valid_request(const sbli_request* r) {
   return SBLI_OK;
 }
 
+int lane_of(int precision) { return req_f64_registers(precision) ? 0 : 1; }
+
 // Final diagnostics and copy-out of a finished request; frees its block.
 int retire(sbli_server* s, Req& q) {
-  cudaStream_t st = req_f64_registers(q.r.precision) ? s->s64 : s->s32;
+  cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
   const Geom g{q.r.n0, q.r.n1, q.r.n2, q.P};
   const int n[3] = {q.r.n0, q.r.n1, q.r.n2};
   const double* state = r64(s, q, q.state);
@@ -305,8 +329,22 @@ int sbli_server_create(sbli_server** out, void* arena, size_t arena_bytes, int m
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  s->grid64 = sms * batch_ctas_per_sm(SBLI_FP64);
-  s->grid32 = sms * batch_ctas_per_sm(SBLI_FP32);
+  s->grid64 = sms * batch_ctas_per_sm(SBLI_FP64, batch_default_zq(SBLI_FP64));
+  s->grid32 = sms * batch_ctas_per_sm(SBLI_FP32, batch_default_zq(SBLI_FP32));
+  s->lane[0].st = s->s64;
+  s->lane[1].st = s->s32;
+  for (Lane& l : s->lane) {
+    if (cudaEventCreate(&l.ev0) != cudaSuccess || cudaEventCreate(&l.ev1) != cudaSuccess) {
+      cudaGetLastError();
+      for (Lane& m : s->lane) {
+        if (m.ev0) cudaEventDestroy(m.ev0);
+        if (m.ev1) cudaEventDestroy(m.ev1);
+      }
+      delete s->alloc;
+      delete s;
+      return sfail(SBLI_ECUDA, "cudaEventCreate failed");
+    }
+  }
   s->t0 = std::chrono::steady_clock::now();
   *out = s;
   return SBLI_OK;
@@ -316,6 +354,10 @@ int sbli_server_destroy(sbli_server* s) {
   if (!s) return SBLI_OK;
   cudaStreamSynchronize(s->s64);
   cudaStreamSynchronize(s->s32);
+  for (Lane& l : s->lane) {
+    cudaEventDestroy(l.ev0);
+    cudaEventDestroy(l.ev1);
+  }
   delete s->alloc;
   delete s;
   return SBLI_OK;
@@ -361,7 +403,7 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     q.t_admit = s->now();
     q.state = 0;
     q.remaining = q.r.steps;
-    cudaStream_t st = req_f64_registers(q.r.precision) ? s->s64 : s->s32;
+    cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
     const Geom qg{q.r.n0, q.r.n1, q.r.n2, q.P};
     if (q.r.precision == SBLI_FP32_DF) {  // binary64 deviation field, then split into hi/lo
       SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 1), st), "init_tgv");
@@ -373,50 +415,75 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     }
     s->active.push_back(q);
   }
-  // one time step for every active request with steps left
-  bool any64 = false, any32 = false, anydw = false, anydf = false;
-  for (const Req& q : s->active) {
-    if (q.remaining > 0)
-      (q.r.precision == SBLI_FP64 ? any64 : q.r.precision == SBLI_DF64 ? anydw
-                                           : q.r.precision == SBLI_FP32_DF ? anydf : any32) = true;
-  }
-  if (any64 || any32 || anydw || anydf) {
-    // requests with no steps left sit out this step
-    std::vector<Req> idle;
-    for (auto it = s->active.begin(); it != s->active.end();) {
-      if (it->remaining == 0) {
-        idle.push_back(*it);
-        it = s->active.erase(it);
-      } else {
-        ++it;
+  int n = 0;
+  // a tick that finds both lanes busy waits (bounded) for the first to finish
+  const auto wait_start = std::chrono::steady_clock::now();
+  for (;;) {
+    bool progressed = false;
+    for (int li = 0; li < 2; ++li) {
+      Lane& L = s->lane[li];
+      if (L.busy) {
+        const cudaError_t q = cudaEventQuery(L.ev1);
+        if (q == cudaErrorNotReady) continue;
+        SBLI_STRY(q, "cudaEventQuery");
+        float ms = 0.f;
+        SBLI_STRY(cudaEventElapsedTime(&ms, L.ev0, L.ev1), "cudaEventElapsedTime");
+        const double per = (double)ms / L.steps;
+        L.ms_per_step = L.ms_per_step > 0 ? 0.5 * (L.ms_per_step + per) : per;
+        L.busy = false;
+        progressed = true;
       }
+      // retire this lane's finished requests (its stream holds no step work now)
+      for (auto it = s->active.begin(); it != s->active.end();) {
+        if (lane_of(it->r.precision) == li && it->remaining == 0) {
+          if (int rc = retire(s, *it)) return rc;
+          s->done.push_back(*it);
+          it = s->active.erase(it);
+          ++n;
+          progressed = true;
+        } else {
+          ++it;
+        }
+      }
+      // next batch: every request of the lane with steps left, K steps
+      std::vector<Req*> run;
+      int kmin = LANE_MAX_STEPS;
+      bool has[4] = {false, false, false, false};
+      for (Req& q : s->active) {
+        if (lane_of(q.r.precision) != li || q.remaining == 0) continue;
+        run.push_back(&q);
+        kmin = std::min(kmin, q.remaining);
+        has[q.r.precision] = true;
+      }
+      if (run.empty()) continue;
+      int K = 1;
+      if (L.ms_per_step > 0) K = (int)std::max(1.0, std::floor(LANE_BATCH_MS / L.ms_per_step));
+      K = std::min(K, kmin);
+      SBLI_STRY(cudaEventRecord(L.ev0, L.st), "cudaEventRecord");
+      for (int step = 0; step < K; ++step) {
+        for (int k = 0; k < 3; ++k) {
+          if (has[SBLI_FP64]) SBLI_STRY(launch_group<double>(s, k, SBLI_FP64, run, L.st, s->grid64), "fp64 stage");
+          if (has[SBLI_DF64])
+            SBLI_STRY(launch_group<dfloat>(s, k, SBLI_DF64, run, L.st, s->grid64), "double-float stage");
+          if (has[SBLI_FP32]) SBLI_STRY(launch_group<float>(s, k, SBLI_FP32, run, L.st, s->grid32), "fp32 stage");
+          if (has[SBLI_FP32_DF])
+            SBLI_STRY(launch_group<float>(s, k, SBLI_FP32_DF, run, L.st, s->grid32), "fp32 double-float stage");
+        }
+        for (Req* q : run) q->state = req_f64_registers(q->r.precision) ? (q->state + 1) % 3 : 1 - q->state;
+      }
+      SBLI_STRY(cudaEventRecord(L.ev1, L.st), "cudaEventRecord");
+      for (Req* q : run) q->remaining -= K;
+      L.busy = true;
+      L.steps = K;
+      progressed = true;
     }
-    for (int k = 0; k < 3; ++k) {
-      if (any64) SBLI_STRY(launch_group<double>(s, k, SBLI_FP64, s->s64, s->grid64), "fp64 stage");
-      if (anydw) SBLI_STRY(launch_group<dfloat>(s, k, SBLI_DF64, s->s64, s->grid64), "double-float stage");
-      if (any32) SBLI_STRY(launch_group<float>(s, k, SBLI_FP32, s->s32, s->grid32), "fp32 stage");
-      if (anydf) SBLI_STRY(launch_group<float>(s, k, SBLI_FP32_DF, s->s32, s->grid32), "fp32 double-float stage");
-    }
-    for (Req& q : s->active) {
-      q.state = req_f64_registers(q.r.precision) ? (q.state + 1) % 3 : 1 - q.state;
-      q.remaining--;
-    }
-    s->active.insert(s->active.end(), idle.begin(), idle.end());
+    if (progressed || (!s->lane[0].busy && !s->lane[1].busy)) break;
+    // nothing to do until a lane finishes: poll its event, at most ~2 ms
+    const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - wait_start).count();
+    if (waited > 0.002) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   s->ticks++;
-  SBLI_STRY(cudaStreamSynchronize(s->s64), "cudaStreamSynchronize");
-  SBLI_STRY(cudaStreamSynchronize(s->s32), "cudaStreamSynchronize");
-  int n = 0;
-  for (auto it = s->active.begin(); it != s->active.end();) {
-    if (it->remaining == 0) {
-      if (int rc = retire(s, *it)) return rc;
-      s->done.push_back(*it);
-      it = s->active.erase(it);
-      ++n;
-    } else {
-      ++it;
-    }
-  }
   if (completed) *completed = n;
   return SBLI_OK;
 }

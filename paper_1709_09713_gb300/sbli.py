@@ -85,6 +85,9 @@ SIGNATURES = {
     "sbli_batch_step_n": (_c_int, [_vp, _c_int, _c_double]),
     "sbli_batch_step_n_history": (_c_int, [_vp, _c_int, _c_double, _vp]),
     "sbli_batch_kinetic_energy": (_c_int, [_vp, _vp, _vp]),
+    "sbli_batch_get_schedule": (_c_int, [_vp, ctypes.POINTER(_c_int), _vp]),
+    "sbli_batch_set_schedule": (_c_int, [_vp, _c_int, _vp]),
+    "sbli_batch_autotune": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float)]),
     "sbli_server_create": (_c_int, [ctypes.POINTER(_vp), _vp, _c_size_t, _c_int, _c_int, _vp, _vp]),
     "sbli_server_destroy": (_c_int, [_vp]),
     "sbli_server_request_bytes": (_c_int, [ctypes.POINTER(Request), ctypes.POINTER(_c_size_t)]),
@@ -278,6 +281,26 @@ def sbli_batch_work_items(h: int) -> int:
     return v.value
 
 
+def sbli_batch_get_schedule(h: int, count: int) -> tuple[int, list[int]]:
+    """(z_queue, planes per work item of each member)."""
+    zq = _c_int()
+    zc = (ctypes.c_int * count)()
+    _check(lib().sbli_batch_get_schedule(_vp(h), ctypes.byref(zq), ctypes.cast(zc, _vp)))
+    return zq.value, list(zc)
+
+
+def sbli_batch_set_schedule(h: int, z_queue: int, planes_per_item=None) -> None:
+    arr = _ints(planes_per_item) if planes_per_item is not None else None
+    _check(lib().sbli_batch_set_schedule(_vp(h), int(z_queue), ctypes.cast(arr, _vp) if arr is not None else None))
+
+
+def sbli_batch_autotune(h: int, reps: int = 3) -> tuple[int, float]:
+    """Tune the batch schedule; returns (z_queue, best stage ms)."""
+    zq, ms = _c_int(), ctypes.c_float()
+    _check(lib().sbli_batch_autotune(_vp(h), int(reps), ctypes.byref(zq), ctypes.byref(ms)))
+    return zq.value, ms.value
+
+
 def sbli_batch_init_tgv(h: int, amplitudes) -> None:
     _check(lib().sbli_batch_init_tgv(_vp(h), ctypes.cast(_doubles(amplitudes), _vp)))
 
@@ -371,6 +394,15 @@ class Batch:
 
     def work_items(self):
         return sbli_batch_work_items(self.handle)
+
+    def schedule(self):
+        return sbli_batch_get_schedule(self.handle, len(self))
+
+    def set_schedule(self, z_queue, planes_per_item=None):
+        sbli_batch_set_schedule(self.handle, z_queue, planes_per_item)
+
+    def autotune(self, reps=3):
+        return sbli_batch_autotune(self.handle, reps)
 
 
 def request(n, precision=SBLI_FP64, steps=10, dt=1e-3, Re=1600.0, Mach=0.1, Pr=0.71, gamma=1.4, L=1.0,

@@ -175,3 +175,50 @@ def test_batch_set_state_mid_run(S, precision):
     assert torch.equal(b.get_state(0), g.get_state())
     g.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_batch_schedules_are_bitwise_identical(S, precision):
+    """The schedule (z-queue mode, planes per work item of each member)
+    changes only the work decomposition: any schedule, and the one the
+    autotuner picks, gives bitwise the state of the default schedule and of
+    each member run alone; the autotuner leaves the state unchanged."""
+    dt, steps = 1e-3, 7
+    ref = S.Batch(SIZES, precision, Re=RE, Mach=MACH)
+    ref.init_tgv(AMP)
+    ref.step_n(steps, dt)
+    want = [ref.get_state(m) for m in range(len(SIZES))]
+    zq0, zc0 = ref.schedule()
+    assert zq0 == (1 if precision in (1, 2) else 0)
+    assert zc0 == [min(32, n[2]) for n in SIZES]
+    ref.close()
+    for sched in [(1 - zq0, [4, 9, 5, 24, 7]), (zq0, [16, 8, 12, 6, 4]), "tuned"]:
+        b = S.Batch(SIZES, precision, Re=RE, Mach=MACH)
+        b.init_tgv(AMP)
+        if sched == "tuned":
+            before = [b.get_state(m) for m in range(len(SIZES))]
+            zq, ms = b.autotune(2)
+            assert zq in (0, 1) and ms > 0
+            for m in range(len(SIZES)):
+                assert torch.equal(b.get_state(m), before[m]), m
+            zq_now, zc_now = b.schedule()
+            assert zq_now == zq and all(4 <= z <= n[2] or z == n[2] for z, n in zip(zc_now, SIZES))
+        else:
+            b.set_schedule(*sched)
+            zq_now, zc_now = b.schedule()
+            assert zq_now == sched[0] and zc_now == [min(z, n[2]) for z, n in zip(sched[1], SIZES)]
+        b.step_n(steps, dt)
+        for m in range(len(SIZES)):
+            assert torch.equal(b.get_state(m), want[m]), (sched, m)
+        b.close()
+
+
+def test_batch_schedule_rejects_bad_values(S):
+    b = S.Batch(SIZES, 1, Re=RE, Mach=MACH)
+    with pytest.raises(S.SbliError) as e:
+        b.set_schedule(2)
+    assert e.value.code == S.SBLI_EINVAL
+    with pytest.raises(S.SbliError) as e:
+        b.set_schedule(1, [4, 4, 3, 4, 4])
+    assert e.value.code == S.SBLI_EINVAL
+    assert b.schedule() == (1, [min(32, n[2]) for n in SIZES])

@@ -117,3 +117,28 @@ def test_server_rejects_bad_requests(S):
         srv.submit(S.request((8, 8, 8), 7, 1))  # unknown precision
     assert e.value.code == S.SBLI_EINVAL
     srv.close()
+
+
+def test_binary32_lane_is_not_gated_by_binary64_steps(S):
+    """The two precision lanes advance independently: a short binary32
+    request admitted beside a long binary64 one finishes while the binary64
+    one is still running, in far less time than the binary64 request needs
+    for the same number of steps (a tick that advanced both lanes together
+    and waited for both would hold every binary32 step to a binary64 step)."""
+    srv = S.Server(1 << 30, max_slots=4)
+    long_id = srv.submit(S.request((160, 160, 160), 0, 40))
+    short_id = srv.submit(S.request((32, 32, 32), 1, 40))
+    done, active_at_short = {}, None
+    for _ in range(100000):
+        srv.tick()
+        for r in srv.poll():
+            done[r.id] = r
+            if r.id == short_id:
+                active_at_short = srv.stats().active
+        if len(done) == 2:
+            break
+    assert len(done) == 2 and active_at_short == 1
+    long_r, short_r = done[long_id], done[short_id]
+    per_step_long = (long_r.t_done - long_r.t_admit) / long_r.steps
+    assert short_r.t_done < long_r.t_done
+    assert short_r.t_done - short_r.t_admit < 0.25 * short_r.steps * per_step_long
