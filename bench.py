@@ -58,15 +58,17 @@ ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "d
 # once the sources differ.
 #   fp64 flop_per_pt: binary64 flop executed (2 DFMA + DADD + DMUL), mean of
 #        the three stages of a 256^3 step; traffic_per_pt: DRAM read + write
-#        bytes per point of one launch, same capture (2.252e9 per launch at
+#        bytes per point of one launch, same capture (2.2477e9 per launch at
 #        256^3; scaled by points to other grids);
-#   df64 inst_per_pt: thread instructions (smsp__inst_executed x 32 / points).
+#   df64 inst_per_pt: thread instructions (smsp__inst_executed x 32 / points),
+#        mean of the three stages of a 256^3 step, per z-queue mode.
 KERNEL_SOURCES = ["fused_stage.cuh", "fused_fp64.cu", "fused_df64.cu", "dfloat.cuh", "fpconv.cuh", "f32x2.cuh",
                   "sbli_internal.cuh"]
 KERNEL_COUNTS = {
-    "fp64": {"flop_per_pt": 572.1, "traffic_per_pt": 2.252e9 / 256**3, "sources": "844c6b84a261",
+    "fp64": {"flop_per_pt": 572.03, "traffic_per_pt": 2.247693e9 / 256**3, "sources": "673a10bb85fb",
              "profile": "profiles/fused_stage_fp64_256.md"},
-    "df64": {"inst_per_pt": 3884.0, "sources": "844c6b84a261", "profile": "profiles/fused_stage_df64_192.md"},
+    "df64": {"inst_per_pt": {0: 3928.4, 1: 3893.8}, "sources": "673a10bb85fb",
+             "profile": "profiles/fused_stage_df64_256.md"},
 }
 
 
@@ -123,6 +125,8 @@ def parse():
                          "--profile-variant) stage by stage; 'algorithms' = stage 0 of every binary64 "
                          "algorithm class at --n; 'ensemble' = --steps steps of the first --profile-members "
                          "members of the seeded ensemble (--profile-precision)")
+    ap.add_argument("--probe", action="store_true",
+                    help="only measure the FMA peaks (binary64, binary32) with the library's probe, clocks sampled")
     ap.add_argument("--profile-members", type=int, default=16)
     ap.add_argument("--profile-precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--profile-variant", default="fused", choices=sorted(VARIANTS))
@@ -390,7 +394,7 @@ def energy_per_pt_stage(g, stream, points, stage_ms, dt, nvml, seconds=1.0):
     g.step_n(steps, dt)
     stream.synchronize()
     e1 = nvml.energy_mj()
-    if e0 is None or e1 is None:
+    if e0 is None or e1 is None or e1 <= e0:
         return None
     return {"j_per_pt_stage": (e1 - e0) / 1e3 / (3.0 * points * steps), "steps": steps,
             "source": "nvmlDeviceGetTotalEnergyConsumption delta over further steps after the timed ones"}
@@ -537,7 +541,13 @@ def leg(S, n, precision, variant, steps, warmup, dt, ws, tune=False, clock_ghz=N
         ach = ALG_BYTES[precision] * P / (stage_ms / 1e3) / 1e9
         out["hbm"] = {"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                       "peak_source": kind, "bytes_per_pt_stage": ALG_BYTES[precision]}
+        if precision == "fp32":
+            # the last stage also writes the binary32 copy of the new state and
+            # stage 0 reads it: 360 B per point-step moved against the 320 B minimum
+            out["hbm"]["bytes_moved_per_pt_stage"] = 120.0
+            out["hbm"]["frac_of_bytes_moved"] = 120.0 * P / (stage_ms / 1e3) / 1e9 / peaks["hbm_gbs"]
         inst = kernel_count("df64", "inst_per_pt") if precision == "df64" else None
+        inst = inst.get(cfg[2]) if inst and cfg else None  # the count of the z-queue mode in use
         if inst and clock_ghz:
             sms = torch.cuda.get_device_properties(0).multi_processor_count
             peak = sms * 4 * 32 * clock_ghz * 1e9
@@ -572,7 +582,7 @@ def algorithms_leg(S, n, steps, warmup, dt, ws, nvml):
         torch.cuda.empty_cache()
         pts = 3.0 * n**3 * steps
         row = {"algorithm": S.VARIANT_NAMES[var], "value": pts * ws / (ms / 1e3), "stage_ms": ms / (3 * steps)}
-        if e0 is not None and e1 is not None:
+        if e0 is not None and e1 is not None and e1 > e0:  # the counter may not advance over a short region
             row["j_per_pt_stage"] = (e1 - e0) / 1e3 / pts
         rows.append(row)
     bl = rows[0]
@@ -675,6 +685,7 @@ def run_ours(args):
                 "hbm_peak_gbs": peaks["hbm_gbs"]}
     elif prec == S.SBLI_DF64 and var == S.SBLI_FUSED:
         inst = kernel_count("df64", "inst_per_pt")
+        inst = inst.get(cfg[2]) if inst and cfg else None
         clock_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = sms * 4 * 32 * clock_ghz * 1e9
@@ -724,7 +735,10 @@ def run_ours(args):
         cg = (clk.get("sm_mhz") or 2070.0) / 1e3
         line["legs"] = [leg(S, 512, "fp32", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
                         leg(S, 512, "fp32df", "fused", args.leg_steps, 2, 5e-4, ws, tune=True, nvml=nvml),
-                        leg(S, 512, "df64", "fused", args.df64_leg_steps, 2, 5e-4, ws, clock_ghz=cg, nvml=nvml),
+                        leg(S, 512, "df64", "fused", args.df64_leg_steps, 2, 5e-4, ws, tune=True, clock_ghz=cg,
+                            nvml=nvml),
+                        leg(S, 256, "df64", "fused", 3 * args.df64_leg_steps, 2, 1e-3, ws, tune=True, clock_ghz=cg,
+                            nvml=nvml),
                         algorithms_leg(S, 256, args.alg_steps, 1, 1e-3, ws, nvml),
                         ensemble_leg(S, args.ens_steps, 6, 1e-3, ws, nvml=nvml),
                         ensemble_leg(S, args.ens_steps, 6, 1e-3, ws, nvml=nvml, precision=S.SBLI_FP32_DF),
@@ -780,9 +794,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_probe(args):
+    """The binary64 and binary32 FMA peaks of this GPU, three times each."""
+    import torch
+
+    from paper_1709_09713_gb300 import build as B
+    from paper_1709_09713_gb300 import sbli as S
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(S.LIB_PATH):
+        B.build()
+    S.lib()
+    out = {"fp64": [], "fp32": []}
+    for name, prec in (("fp64", S.SBLI_FP64), ("fp32", S.SBLI_FP32)):
+        for _ in range(3):
+            r = probe_peak(S, prec, 1.0, 0)
+            out[name].append({"tflops": r["flop_per_s"] / 1e12, "ms": r["ms"], "sm_mhz": r["clocks"].get("sm_mhz"),
+                              "reasons": r["clocks"].get("reasons")})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
-    if args.profile:
+    if args.probe:
+        run_probe(args)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)
