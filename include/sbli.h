@@ -226,8 +226,8 @@ SBLI_API int sbli_get_config(const sbli_grid* g, int* tile_y, int* planes_per_ct
 SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z_queue, int columns_per_thread);
 
 /* Autotuner: times candidate configurations (each allowed tile height, z
- * queue and columns per thread with the planes-per-CTA values a wave-balance
- * model ranks best) on this grid with `reps` timed stage-0 launches each,
+ * queue and columns per thread with the six planes-per-CTA values a
+ * wave-balance model ranks best) on this grid with `reps` timed stage-0 launches each,
  * which read the state and write only the scratch registers, keeps the
  * fastest and returns it.  The state is not changed.  Synchronises the grid's
  * stream.  Fused variant only. */

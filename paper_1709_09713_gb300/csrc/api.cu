@@ -197,7 +197,11 @@ StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
     double* S = g->reg64[state];
     double* A = g->reg64[(state + 1) % 3];
     double* B = g->reg64[(state + 2) % 3];
-    p.in64 = p.out64 = true;
+    // double-float arithmetic: stage fields (B after stage 0, S after stage 1)
+    // are stored as interleaved (hi, lo) binary32 pairs, read by stages 1 and 2
+    const bool pairs = g->precision == SBLI_DF64;
+    p.in64 = !(pairs && k > 0);
+    p.out64 = !pairs;
     if (k == 0) {
       p.q_in = S; p.acc_in = S; p.acc_out = A; p.q_out = B;
     } else if (k == 1) {
@@ -265,7 +269,7 @@ cudaError_t enqueue_stage(sbli_grid* g, int k, int state, double dt, double* ke_
     a.dacc_out = p.dacc_out;
     a.df_normalize = (k == 2);
     if (g->precision == SBLI_FP64) return launch_fused_fp64(a, g->cd, g->cfg, false, s);
-    if (g->precision == SBLI_DF64) return launch_fused_df64(a, g->cw, g->cfg, false, s);
+    if (g->precision == SBLI_DF64) return launch_fused_df64(a, g->cw, g->cfg, false, !p.in64, s);
     if (g->precision == SBLI_FP32_DF) return launch_fused_fp32df(a, g->cf, g->cfg, false, s);
     return launch_fused_fp32(a, g->cf, g->cfg, p.in64, false, s);
   }
@@ -518,6 +522,9 @@ int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host) 
     if (!tmp) return fail(SBLI_EINVAL, "no free register");
     if (src64) {
       SBLI_TRY(launch_from_offset(g->geom, g->ref, static_cast<const double*>(src), tmp, g->stream), "from_offset");
+    } else if (g->precision == SBLI_DF64) {  // interleaved double-float pairs
+      SBLI_TRY(launch_pair_join(5 * g->geom.P, static_cast<const float*>(src), tmp, g->stream), "pair_join");
+      SBLI_TRY(launch_from_offset(g->geom, g->ref, tmp, tmp, g->stream), "from_offset");
     } else {
       SBLI_TRY(launch_widen(5 * g->geom.P, static_cast<const float*>(src), tmp, g->stream), "widen");
       SBLI_TRY(launch_from_offset(g->geom, g->ref, tmp, tmp, g->stream), "from_offset");
@@ -557,7 +564,7 @@ int sbli_rhs(sbli_grid* g, double* r_dev) {
     a.q_in = q;
     a.r_out = r_dev;
     cudaError_t e = g->precision == SBLI_FP64      ? launch_fused_fp64(a, g->cd, g->cfg, true, g->stream)
-                    : g->precision == SBLI_DF64    ? launch_fused_df64(a, g->cw, g->cfg, true, g->stream)
+                    : g->precision == SBLI_DF64    ? launch_fused_df64(a, g->cw, g->cfg, true, false, g->stream)
                     : g->precision == SBLI_FP32_DF ? launch_fused_fp32df(a, g->cf, g->cfg, true, g->stream)
                                                    : launch_fused_fp32(a, g->cf, g->cfg, true, true, g->stream);
     SBLI_TRY(e, "fused rhs launch");
@@ -696,21 +703,22 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int*
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "autotune between stages of a step");
   if (g->variant != SBLI_FUSED) return fail(SBLI_EUNSUPPORTED, "autotune needs the fused variant");
   if (reps < 1) return fail(SBLI_EINVAL, "reps must be >= 1");
-  FusedConfig cand[24];
+  constexpr int ZC_CANDIDATES = 6;  // planes-per-CTA values per kernel shape, best first by the wave model
+  FusedConfig cand[8 * ZC_CANDIDATES];
   int nc = 0;
   const int tys[2] = {8, 16};
   for (int px = 1; px <= 2; ++px)
     for (int zq = 0; zq < 2; ++zq)
       for (int t = 0; t < 2; ++t) {
         if (!valid_config(g->precision, tys[t], 4, zq, px)) continue;
-        int zc[3];
-        rank_zc(g->geom, g->precision, tys[t], zc, 3, px, zq);
-        for (int i = 0; i < 3; ++i) {
+        int zc[ZC_CANDIDATES];
+        rank_zc(g->geom, g->precision, tys[t], zc, ZC_CANDIDATES, px, zq);
+        for (int i = 0; i < ZC_CANDIDATES; ++i) {
           bool dup = false;
           const int z = std::max(4, std::min(zc[i], g->geom.n2));
           for (int j = 0; j < nc; ++j)
             dup |= (cand[j].ty == tys[t] && cand[j].zc == z && cand[j].zq == zq && cand[j].px == px);
-          if (!dup && nc < 24) cand[nc++] = FusedConfig{tys[t], z, zq, px};
+          if (!dup && nc < 8 * ZC_CANDIDATES) cand[nc++] = FusedConfig{tys[t], z, zq, px};
         }
       }
   cudaEvent_t e0, e1;

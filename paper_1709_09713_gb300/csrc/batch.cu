@@ -103,9 +103,12 @@ cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int gr
   return launch_batch_zq<float, float, float, false>(p, grid, s, zq);
 }
 
+// double-float arithmetic members: stage 0 reads the binary64 state, stages 1
+// and 2 stage fields of (hi, lo) pairs; stage fields are written as pairs
 template <>
-cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool, int grid, cudaStream_t s, bool, int zq) {
-  return launch_batch_zq<dfloat, double, double, false>(p, grid, s, zq);
+cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool in64, int grid, cudaStream_t s, bool, int zq) {
+  if (in64) return launch_batch_zq<dfloat, double, dfloat, false>(p, grid, s, zq);
+  return launch_batch_zq<dfloat, dfloat, dfloat, false>(p, grid, s, zq);
 }
 
 template <>
@@ -245,7 +248,8 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
     double* S = r64(state);
     double* A = r64((state + 1) % 3);
     double* B = r64((state + 2) % 3);
-    *in64 = true;
+    // double-float arithmetic: stages 1 and 2 read stage fields of (hi, lo) pairs
+    *in64 = !(b->precision == SBLI_DF64 && k > 0);
     if (k == 0) { a.q_in = S; a.acc_in = S; a.acc_out = A; a.q_out = B; }
     else if (k == 1) { a.q_in = B; a.acc_in = A; a.acc_out = A; a.q_out = S; }
     else { a.q_in = S; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }

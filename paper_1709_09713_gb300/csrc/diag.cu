@@ -156,6 +156,20 @@ cudaError_t launch_df_join(long long P, const RefState& r, const float* src, dou
   return cudaGetLastError();
 }
 
+// A stage field of interleaved double-float pairs as binary64 (the sum of two
+// binary32 values is exact in binary64).
+__global__ void pair_join_kernel(long long n, const float2* __restrict__ src, double* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    dst[i] = (double)v.x + (double)v.y;
+  }
+}
+
+cudaError_t launch_pair_join(long long n, const float* src, double* dst, cudaStream_t s) {
+  pair_join_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, reinterpret_cast<const float2*>(src), dst);
+  return cudaGetLastError();
+}
+
 // Plain conserved variables at listed points: out[f * count + i] for the
 // point of linear index idx[i] (x0 fastest).  The binary64 state (q64) or the
 // double-float state (qdf: hi fields, then lo fields) is in deviation form;

@@ -1,24 +1,30 @@
 // fused_df64.cu -- the fused stage kernel with binary64 storage and
-// double-float arithmetic (dfloat.cuh): stage inputs are split into
-// hi + lo binary32 pairs when a plane enters the ring, every derivative and
-// the residual run on the binary32 pipe, and the Runge-Kutta update of the
-// binary64 registers is the binary64 FMA of the binary64 path.
+// double-float arithmetic (dfloat.cuh): the state and accumulator are
+// binary64; stage 0 splits each loaded binary64 value into a hi + lo binary32
+// pair when its plane enters the ring, and stages 0 and 1 write their stage
+// field already split (interleaved hi, lo pairs in the register's bytes), so
+// stages 1 and 2 read pairs; every derivative and the residual run on the
+// binary32 pipe, and the Runge-Kutta update of the binary64 accumulator is
+// the binary64 FMA of the binary64 path.
 #include "fused_stage.cuh"
 
 namespace sbli {
 
 template <int TY, bool ZT>
-static cudaError_t dispatch_df64(const StageArgs& a, const Coef<dfloat>& c, bool rhs_only, cudaStream_t s) {
+static cudaError_t dispatch_df64(const StageArgs& a, const Coef<dfloat>& c, bool rhs_only, bool in_pairs,
+                                 cudaStream_t s) {
   if (rhs_only) return launch_fused_t<dfloat, double, double, TY, true, false, false, ZT>(a, c, s);
-  if (a.ke_partials) return launch_fused_t<dfloat, double, double, TY, false, true, false, ZT>(a, c, s);
-  return launch_fused_t<dfloat, double, double, TY, false, false, false, ZT>(a, c, s);
+  if (in_pairs) return launch_fused_t<dfloat, dfloat, dfloat, TY, false, false, false, ZT>(a, c, s);
+  if (a.ke_partials) return launch_fused_t<dfloat, double, dfloat, TY, false, true, false, ZT>(a, c, s);
+  return launch_fused_t<dfloat, double, dfloat, TY, false, false, false, ZT>(a, c, s);
 }
 
 cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
-                              cudaStream_t s) {
+                              bool in_pairs, cudaStream_t s) {
   switch (cfg.ty) {
     case 8:
-      return cfg.zq ? dispatch_df64<8, true>(a, c, rhs_only, s) : dispatch_df64<8, false>(a, c, rhs_only, s);
+      return cfg.zq ? dispatch_df64<8, true>(a, c, rhs_only, in_pairs, s)
+                    : dispatch_df64<8, false>(a, c, rhs_only, in_pairs, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -408,6 +408,18 @@ __device__ __forceinline__ dfloat to_compute<dfloat, double>(double v) {
   return dfloat(hi, narrow_f64_fast(v - widen_f32_fast(hi)));
 }
 
+// A binary64 stage output in the stored type: itself, or (double-float
+// stage fields) the same hi + lo split a binary64 input gets when it is
+// loaded, so the consumer reads the pair it would have formed.
+template <typename TOUT>
+__device__ __forceinline__ TOUT to_output(double v) {
+  return TOUT(v);
+}
+template <>
+__device__ __forceinline__ dfloat to_output<dfloat>(double v) {
+  return to_compute<dfloat, double>(v);
+}
+
 // a * b + c: left to the compiler's contraction for scalar types, an explicit
 // packed FMA for f32x2 (whose operators are not contracted)
 template <typename T>
@@ -1003,7 +1015,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           for (int f = 0; f < NF; ++f) {
             const double r = as_double(R[f]);
             a.acc_out[(long long)f * a.g.P + o] = fma(a.b_dt, r, accv[f][j]);
-            qo[f] = TOUT(fma(a.a_dt, r, accv[f][j]));
+            qo[f] = to_output<TOUT>(fma(a.a_dt, r, accv[f][j]));
           }
         } else {
           // binary32 stage, binary64 accumulator: one DADD per field,

@@ -98,9 +98,12 @@ cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const Fu
 // binary32 stage with a double-float accumulator (stage inputs are binary32)
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s);
-// binary64 storage, double-float arithmetic (fused_df64.cu)
+// binary64 storage, double-float arithmetic (fused_df64.cu): the stage
+// input is the binary64 state (in_pairs false: stage 0 and the residual) or
+// a stage field of interleaved (hi, lo) binary32 pairs (stages 1 and 2); the
+// stage output field is written as pairs.
 cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
-                              cudaStream_t s);
+                              bool in_pairs, cudaStream_t s);
 // the two binary32 paths with two columns per thread (fused_fp32_pair.cu)
 cudaError_t launch_fused_fp32_pair(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool in_fp64,
                                    bool df, bool rhs_only, cudaStream_t s);
@@ -124,6 +127,9 @@ cudaError_t launch_narrow(long long n, const double* src, float* dst, cudaStream
 // zero RefState to stay in deviation form.
 cudaError_t launch_df_split(long long P, const RefState& r, const double* src, float* dst, cudaStream_t s);
 cudaError_t launch_df_join(long long P, const RefState& r, const float* src, double* dst, cudaStream_t s);
+// dst[i] = (double)src[2i] + (double)src[2i+1], i < n (exact): a stage field of
+// interleaved double-float pairs (binary64-register double-float grids) as binary64
+cudaError_t launch_pair_join(long long n, const float* src, double* dst, cudaStream_t s);
 // Gather the plain conserved variables of count points (q64: binary64 state,
 // or qdf: double-float state) into out[5][count]; NaN for indices outside [0, P).
 cudaError_t launch_sample_state(long long P, const RefState& r, const double* q64, const float* qdf,

@@ -186,7 +186,8 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
     double* S = r64(s, q, st);
     double* A = r64(s, q, (st + 1) % 3);
     double* B = r64(s, q, (st + 2) % 3);
-    *in64 = true;
+    // double-float arithmetic: stages 1 and 2 read stage fields of (hi, lo) pairs
+    *in64 = !(q.r.precision == SBLI_DF64 && k > 0);
     if (k == 0) { a.q_in = S; a.acc_in = S; a.acc_out = A; a.q_out = B; }
     else if (k == 1) { a.q_in = B; a.acc_in = A; a.acc_out = A; a.q_out = S; }
     else { a.q_in = S; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
