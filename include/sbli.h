@@ -29,11 +29,13 @@
  *    and the state between steps are double-float pairs (hi + lo, two
  *    binary32, about 48 significant bits) updated with error-free binary32
  *    additions, so no binary64 arithmetic runs in the stages (fused variant;
- *    single grids, batches and requests).  Precision SBLI_DF64: binary64 registers, state and
- *    accumulator exactly as SBLI_FP64, but the stage arithmetic (primitives,
+ *    single grids, batches and requests).  Precision SBLI_DF64: binary64 state and
+ *    accumulator as SBLI_FP64, but the stage arithmetic (primitives,
  *    derivatives, residual) in double-float: each value a hi + lo pair of
  *    binary32 (about 48 significant bits) evaluated on the binary32 pipe with
- *    error-free transformations; the RK update is the binary64 FMA (fused
+ *    error-free transformations; the RK update is the binary64 FMA.  The
+ *    stage fields, and on single grids a copy of the state, are stored as
+ *    those (hi, lo) pairs, split once by the stage that writes them (fused
  *    variant; single grids, batches and requests).  All store the state as deviations from the uniform
  *    reference state (rho = 1, u = 0, p = 1/(gamma M^2)); the
  *    get/set calls convert to and from the plain conserved variables.
@@ -144,7 +146,8 @@ SBLI_API int sbli_sample_state(sbli_grid* g, const long long* idx_dev, int count
 
 /* Between the stages of a step (after stage 0 or 1): copy out the next
  * stage's input field Q_k and the accumulator Q_acc as 5*n0*n1*n2 binary64
- * plain conserved variables (binary32 stage fields are widened).  For
+ * plain conserved variables (binary32 stage fields are widened, double-float
+ * pair fields joined exactly).  For
  * verifying single stages.  Either pointer may be NULL.  q_is_host as in
  * sbli_get_state (host copies synchronise). */
 SBLI_API int sbli_get_stage(sbli_grid* g, double* q_stage, double* q_acc, int q_is_host);

@@ -121,6 +121,20 @@ struct sbli_grid {
 
 namespace {
 
+// Where a grid keeps its binary64 state between steps.  Double-float grids
+// (SBLI_DF64) keep the state and accumulator in reg64[0], updated in place
+// by every stage, and the (hi, lo) pair copy of the state in reg64[state]
+// (1 or 2): the stages read only pair fields as stencil input, so the
+// accumulator is read pointwise and may be overwritten in place.  Every other
+// precision keeps the state in reg64[state].
+double* state64(const sbli_grid* g) { return g->precision == SBLI_DF64 ? g->reg64[0] : g->reg64[g->state]; }
+int initial_state(int precision) { return precision == SBLI_DF64 ? 1 : 0; }
+// a binary64 register that holds nothing live at a step boundary
+double* free64(const sbli_grid* g) {
+  if (g->precision == SBLI_DF64) return g->reg64[3 - g->state];
+  return g->reg64[(g->state + 1) % g->layout.n64];
+}
+
 // CTAs per SM a tile height allows (shared memory bound).
 int ctas_per_sm(int precision, int ty, int px = 1, int zq = 0) {
   if (f64_registers(precision) || ty >= 16 || px == 2) return 1;
@@ -193,15 +207,28 @@ struct StagePtrs {
 
 StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
   StagePtrs p{};
-  if (f64_registers(g->precision)) {
+  if (g->precision == SBLI_DF64) {
+    // double-float arithmetic: accumulator S updated in place; the stage
+    // fields alternate between the two pair registers, Pa holding the pair
+    // copy of Q^n at the step boundary (written by the previous stage 2)
+    double* S = g->reg64[0];
+    double* Pa = g->reg64[state];
+    double* Pb = g->reg64[3 - state];
+    p.in64 = p.out64 = false;
+    p.acc_in = S;
+    p.acc_out = S;
+    if (k == 0) {
+      p.q_in = Pa; p.q_out = Pb;
+    } else if (k == 1) {
+      p.q_in = Pb; p.q_out = Pa;
+    } else {
+      p.q_in = Pa; p.q_out = Pb;  // a_3 = b_3: the pair copy of Q^{n+1}
+    }
+  } else if (f64_registers(g->precision)) {
     double* S = g->reg64[state];
     double* A = g->reg64[(state + 1) % 3];
     double* B = g->reg64[(state + 2) % 3];
-    // double-float arithmetic: stage fields (B after stage 0, S after stage 1)
-    // are stored as interleaved (hi, lo) binary32 pairs, read by stages 1 and 2
-    const bool pairs = g->precision == SBLI_DF64;
-    p.in64 = !(pairs && k > 0);
-    p.out64 = !pairs;
+    p.in64 = p.out64 = true;
     if (k == 0) {
       p.q_in = S; p.acc_in = S; p.acc_out = A; p.q_out = B;
     } else if (k == 1) {
@@ -244,7 +271,10 @@ StagePtrs stage_ptrs(const sbli_grid* g, int k, int state) {
   return p;
 }
 
-int next_state(const sbli_grid* g, int state) { return f64_registers(g->precision) ? (state + 1) % 3 : 1 - state; }
+int next_state(const sbli_grid* g, int state) {
+  if (g->precision == SBLI_DF64) return 3 - state;
+  return f64_registers(g->precision) ? (state + 1) % 3 : 1 - state;
+}
 
 // Enqueue stage k on stream s for the given rotation; ke_partials != nullptr
 // (stage 0 only) also accumulates the diagnostics of the stage input.
@@ -397,7 +427,7 @@ int sbli_create_grid(sbli_grid** out, int n0, int n1, int n2, int precision, int
   g->ke_out = g->partials + (g->layout.partials / sizeof(double) - 2);
   w += g->layout.partials;
   g->storeall = g->layout.storeall ? static_cast<void*>(w) : nullptr;
-  g->state = 0;
+  g->state = initial_state(precision);
   g->next_stage = 0;
   g->stages_done = 0;
   g->cfg = default_config(g->geom, precision);
@@ -426,7 +456,7 @@ int sbli_destroy_grid(sbli_grid* g) {
 int sbli_init_tgv(sbli_grid* g, double amplitude) {
   if (int rc = check_grid(g)) return rc;
   if (!isfinite(amplitude)) return fail(SBLI_EINVAL, "amplitude must be finite");
-  g->state = 0;
+  g->state = initial_state(g->precision);
   g->next_stage = 0;
   g->stages_done = 0;
   if (g->precision == SBLI_FP32_DF) {
@@ -440,6 +470,9 @@ int sbli_init_tgv(sbli_grid* g, double amplitude) {
   SBLI_TRY(launch_init_tgv(g->geom, g->params, amplitude, g->reg64[0], g->stream), "init_tgv launch");
   if (g->precision == SBLI_FP32)
     SBLI_TRY(launch_narrow(5 * g->geom.P, g->reg64[0], g->reg32[0], g->stream), "narrow launch");
+  if (g->precision == SBLI_DF64)
+    SBLI_TRY(launch_pair_split(5 * g->geom.P, g->reg64[0], reinterpret_cast<float*>(g->reg64[g->state]), g->stream),
+             "pair_split launch");
   return SBLI_OK;
 }
 
@@ -450,7 +483,7 @@ int sbli_set_state(sbli_grid* g, const double* q, int q_is_host) {
   const size_t bytes = 5 * (size_t)g->geom.P * sizeof(double);
   // stage through a free register, then convert to deviation form
   const int dst = g->state;
-  double* tmp = g->reg64[(dst + 1) % g->layout.n64];
+  double* tmp = free64(g);
   if (q_is_host) {
     SBLI_TRY(cudaMemcpyAsync(tmp, q, bytes, cudaMemcpyHostToDevice, g->stream), "cudaMemcpyAsync H2D");
   } else {
@@ -459,9 +492,12 @@ int sbli_set_state(sbli_grid* g, const double* q, int q_is_host) {
   if (g->precision == SBLI_FP32_DF) {
     SBLI_TRY(launch_df_split(g->geom.P, g->ref, tmp, reinterpret_cast<float*>(g->reg64[dst]), g->stream), "df_split");
   } else {
-    SBLI_TRY(launch_to_offset(g->geom, g->ref, tmp, g->reg64[dst], g->stream), "to_offset launch");
+    SBLI_TRY(launch_to_offset(g->geom, g->ref, tmp, state64(g), g->stream), "to_offset launch");
     if (g->precision == SBLI_FP32)
       SBLI_TRY(launch_narrow(5 * g->geom.P, g->reg64[dst], g->reg32[dst], g->stream), "narrow launch");
+    if (g->precision == SBLI_DF64)
+      SBLI_TRY(launch_pair_split(5 * g->geom.P, state64(g), reinterpret_cast<float*>(g->reg64[dst]), g->stream),
+               "pair_split launch");
   }
   if (q_is_host) SBLI_TRY(cudaStreamSynchronize(g->stream), "cudaStreamSynchronize");
   g->stages_done = 0;
@@ -473,12 +509,12 @@ int sbli_get_state(sbli_grid* g, double* q, int q_is_host) {
   if (!q) return fail(SBLI_EINVAL, "q is null");
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "get_state between stages of a step (next stage %d)", g->next_stage);
   const size_t bytes = 5 * (size_t)g->geom.P * sizeof(double);
-  double* tmp = g->reg64[(g->state + 1) % g->layout.n64];
+  double* tmp = free64(g);
   if (g->precision == SBLI_FP32_DF) {
     SBLI_TRY(launch_df_join(g->geom.P, g->ref, reinterpret_cast<const float*>(g->reg64[g->state]), tmp, g->stream),
              "df_join");
   } else {
-    SBLI_TRY(launch_from_offset(g->geom, g->ref, g->reg64[g->state], tmp, g->stream), "from_offset launch");
+    SBLI_TRY(launch_from_offset(g->geom, g->ref, state64(g), tmp, g->stream), "from_offset launch");
   }
   if (q_is_host) {
     SBLI_TRY(cudaMemcpyAsync(q, tmp, bytes, cudaMemcpyDeviceToHost, g->stream), "cudaMemcpyAsync D2H");
@@ -496,7 +532,7 @@ int sbli_sample_state(sbli_grid* g, const long long* idx_dev, int count, double*
   if (!idx_dev || !out_dev) return fail(SBLI_EINVAL, "idx_dev or out_dev is null");
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "sample_state between stages of a step (next stage %d)", g->next_stage);
   const bool df = g->precision == SBLI_FP32_DF;
-  const double* q64 = df ? nullptr : g->reg64[g->state];
+  const double* q64 = df ? nullptr : state64(g);
   const float* qdf = df ? reinterpret_cast<const float*>(g->reg64[g->state]) : nullptr;
   SBLI_TRY(launch_sample_state(g->geom.P, g->ref, q64, qdf, idx_dev, count, out_dev, g->stream), "sample_state launch");
   return SBLI_OK;
@@ -556,7 +592,7 @@ int sbli_rhs(sbli_grid* g, double* r_dev) {
   if (int rc = check_grid(g)) return rc;
   if (!r_dev) return fail(SBLI_EINVAL, "r_dev is null");
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "rhs between stages of a step");
-  const double* q = g->reg64[g->state];
+  const double* q = state64(g);
   if (g->variant == SBLI_FUSED) {
     StageArgs a{};
     a.g = g->geom;
@@ -644,7 +680,7 @@ int sbli_kinetic_energy_async(sbli_grid* g, double* out_dev) {
   if (int rc = check_grid(g)) return rc;
   if (!out_dev) return fail(SBLI_EINVAL, "out_dev is null");
   if (g->next_stage != 0) return fail(SBLI_EINVAL, "kinetic_energy between stages of a step");
-  const double* q = g->reg64[g->state];
+  const double* q = state64(g);
   if (g->precision == SBLI_FP32_DF) {
     double* tmp = g->reg64[1 - g->state];  // free at a step boundary
     const RefState zero{0.0, 0.0};

@@ -156,6 +156,21 @@ cudaError_t launch_df_join(long long P, const RefState& r, const float* src, dou
   return cudaGetLastError();
 }
 
+// A binary64 field as interleaved double-float pairs, split as the stage
+// kernels split a binary64 input (split_f64).
+__global__ void pair_split_kernel(long long n, const double* __restrict__ src, float2* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float hi, lo;
+    split_f64(src[i], hi, lo);
+    dst[i] = make_float2(hi, lo);
+  }
+}
+
+cudaError_t launch_pair_split(long long n, const double* src, float* dst, cudaStream_t s) {
+  pair_split_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, src, reinterpret_cast<float2*>(dst));
+  return cudaGetLastError();
+}
+
 // A stage field of interleaved double-float pairs as binary64 (the sum of two
 // binary32 values is exact in binary64).
 __global__ void pair_join_kernel(long long n, const float2* __restrict__ src, double* __restrict__ dst) {

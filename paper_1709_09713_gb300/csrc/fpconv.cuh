@@ -95,4 +95,14 @@ __device__ __forceinline__ float narrow_f64_rna(double d) {
   return __uint_as_float(bits);
 }
 
+// binary64 -> double-float pair: hi = RN32(v), lo = RN32(v - hi); the
+// narrowings and the widening of hi are integer re-packings, the remainder one
+// DADD (exact: v - hi has at most 29 significant bits).  The stage kernels
+// split binary64 stage inputs this way, and the double-float path stores its
+// stage fields already split this way.
+__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
+  hi = narrow_f64_fast(v);
+  lo = narrow_f64_fast(v - widen_f32_fast(hi));
+}
+
 }  // namespace sbli

@@ -1,11 +1,12 @@
 // fused_df64.cu -- the fused stage kernel with binary64 storage and
 // double-float arithmetic (dfloat.cuh): the state and accumulator are
-// binary64; stage 0 splits each loaded binary64 value into a hi + lo binary32
-// pair when its plane enters the ring, and stages 0 and 1 write their stage
-// field already split (interleaved hi, lo pairs in the register's bytes), so
-// stages 1 and 2 read pairs; every derivative and the residual run on the
-// binary32 pipe, and the Runge-Kutta update of the binary64 accumulator is
-// the binary64 FMA of the binary64 path.
+// binary64, updated in place; every stage reads its stencil input as
+// interleaved (hi, lo) binary32 pairs (the split a binary64 value gets, done
+// once by the stage that writes the field: stages 0 and 1 write the next
+// stage's field, stage 2 the pair copy of the new state, which the next step's
+// stage 0 reads); every derivative and the residual run on the binary32 pipe,
+// and the Runge-Kutta update of the binary64 accumulator is the binary64 FMA
+// of the binary64 path.  The residual alone reads the binary64 state.
 #include "fused_stage.cuh"
 
 namespace sbli {
@@ -14,9 +15,9 @@ template <int TY, bool ZT>
 static cudaError_t dispatch_df64(const StageArgs& a, const Coef<dfloat>& c, bool rhs_only, bool in_pairs,
                                  cudaStream_t s) {
   if (rhs_only) return launch_fused_t<dfloat, double, double, TY, true, false, false, ZT>(a, c, s);
-  if (in_pairs) return launch_fused_t<dfloat, dfloat, dfloat, TY, false, false, false, ZT>(a, c, s);
-  if (a.ke_partials) return launch_fused_t<dfloat, double, dfloat, TY, false, true, false, ZT>(a, c, s);
-  return launch_fused_t<dfloat, double, dfloat, TY, false, false, false, ZT>(a, c, s);
+  if (!in_pairs) return cudaErrorInvalidValue;  // single-grid stages read pair fields
+  if (a.ke_partials) return launch_fused_t<dfloat, dfloat, dfloat, TY, false, true, false, ZT>(a, c, s);
+  return launch_fused_t<dfloat, dfloat, dfloat, TY, false, false, false, ZT>(a, c, s);
 }
 
 cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,

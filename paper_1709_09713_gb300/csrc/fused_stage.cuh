@@ -404,8 +404,9 @@ __device__ __forceinline__ float to_compute<float, double>(double v) {
 // (exact: v - hi has at most 29 significant bits)
 template <>
 __device__ __forceinline__ dfloat to_compute<dfloat, double>(double v) {
-  const float hi = narrow_f64_fast(v);
-  return dfloat(hi, narrow_f64_fast(v - widen_f32_fast(hi)));
+  float hi, lo;
+  split_f64(v, hi, lo);
+  return dfloat(hi, lo);
 }
 
 // A binary64 stage output in the stored type: itself, or (double-float

@@ -98,10 +98,10 @@ cudaError_t launch_fused_fp32(const StageArgs& a, const Coef<float>& c, const Fu
 // binary32 stage with a double-float accumulator (stage inputs are binary32)
 cudaError_t launch_fused_fp32df(const StageArgs& a, const Coef<float>& c, const FusedConfig& cfg, bool rhs_only,
                                 cudaStream_t s);
-// binary64 storage, double-float arithmetic (fused_df64.cu): the stage
-// input is the binary64 state (in_pairs false: stage 0 and the residual) or
-// a stage field of interleaved (hi, lo) binary32 pairs (stages 1 and 2); the
-// stage output field is written as pairs.
+// binary64 storage, double-float arithmetic (fused_df64.cu): the stage input
+// is a field of interleaved (hi, lo) binary32 pairs (in_pairs: every stage of
+// a single grid) or the binary64 state (the residual alone); the stage output
+// field is written as pairs.
 cudaError_t launch_fused_df64(const StageArgs& a, const Coef<dfloat>& c, const FusedConfig& cfg, bool rhs_only,
                               bool in_pairs, cudaStream_t s);
 // the two binary32 paths with two columns per thread (fused_fp32_pair.cu)
@@ -130,6 +130,8 @@ cudaError_t launch_df_join(long long P, const RefState& r, const float* src, dou
 // dst[i] = (double)src[2i] + (double)src[2i+1], i < n (exact): a stage field of
 // interleaved double-float pairs (binary64-register double-float grids) as binary64
 cudaError_t launch_pair_join(long long n, const float* src, double* dst, cudaStream_t s);
+// dst[2i], dst[2i+1] = the double-float split of src[i] (split_f64), i < n
+cudaError_t launch_pair_split(long long n, const double* src, float* dst, cudaStream_t s);
 // Gather the plain conserved variables of count points (q64: binary64 state,
 // or qdf: double-float state) into out[5][count]; NaN for indices outside [0, P).
 cudaError_t launch_sample_state(long long P, const RefState& r, const double* q64, const float* qdf,
