@@ -770,10 +770,12 @@ int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int*
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < nc && err == cudaSuccess; ++i) {
     g->cfg = cand[i];
-    // stage 0 reads the state and writes only the two other registers
-    err = enqueue_stage(g, 0, g->state, 1e-6, nullptr, g->stream);
+    // stage 0 with dt = 0: the accumulator it writes equals the state it
+    // reads (acc + 0 * R), so a double-float grid's state, updated in place,
+    // keeps its value; the stage field goes to a free register
+    err = enqueue_stage(g, 0, g->state, 0.0, nullptr, g->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e0, g->stream);
-    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = enqueue_stage(g, 0, g->state, 1e-6, nullptr, g->stream);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = enqueue_stage(g, 0, g->state, 0.0, nullptr, g->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e1, g->stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0.f;

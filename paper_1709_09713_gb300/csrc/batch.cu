@@ -103,11 +103,11 @@ cudaError_t launch_batch_t<float>(const BatchParams<float>& p, bool in64, int gr
   return launch_batch_zq<float, float, float, false>(p, grid, s, zq);
 }
 
-// double-float arithmetic members: stage 0 reads the binary64 state, stages 1
-// and 2 stage fields of (hi, lo) pairs; stage fields are written as pairs
+// double-float arithmetic members: every stage reads a field of (hi, lo)
+// pairs and writes its stage field as pairs
 template <>
 cudaError_t launch_batch_t<dfloat>(const BatchParams<dfloat>& p, bool in64, int grid, cudaStream_t s, bool, int zq) {
-  if (in64) return launch_batch_zq<dfloat, double, dfloat, false>(p, grid, s, zq);
+  if (in64) return cudaErrorInvalidValue;
   return launch_batch_zq<dfloat, dfloat, dfloat, false>(p, grid, s, zq);
 }
 
@@ -226,7 +226,17 @@ struct sbli_batch {
 
 namespace {
 
-int batch_next_state(const sbli_batch* b, int s) { return batch_f64_registers(b->precision) ? (s + 1) % 3 : 1 - s; }
+// Double-float members (SBLI_DF64) keep their binary64 state and accumulator
+// in register 0, updated in place, and the (hi, lo) pair copy of the state in
+// register `state` (1 or 2), as single grids do; every other precision keeps
+// its state in register `state`.
+int batch_initial_state(int precision) { return precision == SBLI_DF64 ? 1 : 0; }
+int batch_next_state(const sbli_batch* b, int s) {
+  if (b->precision == SBLI_DF64) return 3 - s;
+  return batch_f64_registers(b->precision) ? (s + 1) % 3 : 1 - s;
+}
+int state_reg(const sbli_batch* b) { return b->precision == SBLI_DF64 ? 0 : b->state; }
+int free_reg(const sbli_batch* b) { return b->precision == SBLI_DF64 ? 3 - b->state : (b->state + 1) % b->L.n64; }
 
 Geom member_geom(const MemberLayout& M) { return Geom{M.n[0], M.n[1], M.n[2], M.P}; }
 
@@ -244,12 +254,23 @@ StageArgs member_stage(const sbli_batch* b, int m, int k, int state, double dt, 
   a.df_normalize = (k == 2);
   auto r64 = [&](int r) { return reinterpret_cast<double*>(b->reg64[r] + M.off64); };
   auto r32 = [&](int r) { return reinterpret_cast<float*>(b->reg32[r] + M.off32); };
-  if (batch_f64_registers(b->precision)) {
+  if (b->precision == SBLI_DF64) {
+    // accumulator in place in register 0; stage fields of (hi, lo) pairs
+    // alternate between registers `state` (the pair copy of Q^n) and 3 - state
+    double* S = r64(0);
+    double* Pa = r64(state);
+    double* Pb = r64(3 - state);
+    *in64 = false;
+    a.acc_in = S;
+    a.acc_out = S;
+    if (k == 0) { a.q_in = Pa; a.q_out = Pb; }
+    else if (k == 1) { a.q_in = Pb; a.q_out = Pa; }
+    else { a.q_in = Pa; a.q_out = Pb; }  // a_3 = b_3: the pair copy of Q^{n+1}
+  } else if (batch_f64_registers(b->precision)) {
     double* S = r64(state);
     double* A = r64((state + 1) % 3);
     double* B = r64((state + 2) % 3);
-    // double-float arithmetic: stages 1 and 2 read stage fields of (hi, lo) pairs
-    *in64 = !(b->precision == SBLI_DF64 && k > 0);
+    *in64 = true;
     if (k == 0) { a.q_in = S; a.acc_in = S; a.acc_out = A; a.q_out = B; }
     else if (k == 1) { a.q_in = B; a.acc_in = A; a.acc_out = A; a.q_out = S; }
     else { a.q_in = S; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
@@ -432,7 +453,7 @@ int sbli_batch_create(sbli_batch** out, int count, const int* n, const sbli_para
   b->begin = reinterpret_cast<long long*>(w);
   w += balign((size_t)(count + 1) * sizeof(long long));
   b->ke_scratch = reinterpret_cast<double*>(w);
-  b->state = 0;
+  b->state = batch_initial_state(b->precision);
   b->steps_done = 0;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -472,7 +493,7 @@ int sbli_batch_count(const sbli_batch* b, int* count) {
 int sbli_batch_init_tgv(sbli_batch* b, const double* amplitudes) {
   if (int rc = check_batch(b, 0)) return rc;
   if (!amplitudes) return bfail(SBLI_EINVAL, "amplitudes is null");
-  b->state = 0;
+  b->state = batch_initial_state(b->precision);
   b->steps_done = 0;
   for (int m = 0; m < b->count; ++m) {
     if (!isfinite(amplitudes[m])) return bfail(SBLI_EINVAL, "amplitude %d not finite", m);
@@ -489,6 +510,10 @@ int sbli_batch_init_tgv(sbli_batch* b, const double* amplitudes) {
     SBLI_BTRY(launch_init_tgv(member_geom(M), b->params[m], amplitudes[m],
                               reinterpret_cast<double*>(b->reg64[0] + M.off64), b->stream),
               "init_tgv");
+    if (b->precision == SBLI_DF64)
+      SBLI_BTRY(launch_pair_split(5 * M.P, reinterpret_cast<double*>(b->reg64[0] + M.off64),
+                                  reinterpret_cast<float*>(b->reg64[b->state] + M.off64), b->stream),
+                "pair_split");
     if (b->precision == SBLI_FP32)
       SBLI_BTRY(launch_narrow(5 * M.P, reinterpret_cast<double*>(b->reg64[0] + M.off64),
                               reinterpret_cast<float*>(b->reg32[0] + M.off32), b->stream),
@@ -501,8 +526,8 @@ int sbli_batch_set_state(sbli_batch* b, int member, const double* q, int q_is_ho
   if (int rc = check_batch(b, member)) return rc;
   if (!q) return bfail(SBLI_EINVAL, "q is null");
   const MemberLayout& M = b->L.m[member];
-  double* dst = reinterpret_cast<double*>(b->reg64[b->state] + M.off64);
-  double* tmp = reinterpret_cast<double*>(b->reg64[(b->state + 1) % b->L.n64] + M.off64);
+  double* dst = reinterpret_cast<double*>(b->reg64[state_reg(b)] + M.off64);
+  double* tmp = reinterpret_cast<double*>(b->reg64[free_reg(b)] + M.off64);
   SBLI_BTRY(cudaMemcpyAsync(tmp, q, 5 * M.P * sizeof(double), q_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             b->stream),
             "cudaMemcpyAsync");
@@ -511,6 +536,9 @@ int sbli_batch_set_state(sbli_batch* b, int member, const double* q, int q_is_ho
               "df_split");
   } else {
     SBLI_BTRY(launch_to_offset(member_geom(M), make_ref(b->params[member]), tmp, dst, b->stream), "to_offset");
+    if (b->precision == SBLI_DF64)
+      SBLI_BTRY(launch_pair_split(5 * M.P, dst, reinterpret_cast<float*>(b->reg64[b->state] + M.off64), b->stream),
+                "pair_split");
     if (b->precision == SBLI_FP32)
       SBLI_BTRY(launch_narrow(5 * M.P, dst, reinterpret_cast<float*>(b->reg32[b->state] + M.off32), b->stream),
                 "narrow");
@@ -523,8 +551,8 @@ int sbli_batch_get_state(sbli_batch* b, int member, double* q, int q_is_host) {
   if (int rc = check_batch(b, member)) return rc;
   if (!q) return bfail(SBLI_EINVAL, "q is null");
   const MemberLayout& M = b->L.m[member];
-  const double* src = reinterpret_cast<double*>(b->reg64[b->state] + M.off64);
-  double* tmp = reinterpret_cast<double*>(b->reg64[(b->state + 1) % b->L.n64] + M.off64);
+  const double* src = reinterpret_cast<double*>(b->reg64[state_reg(b)] + M.off64);
+  double* tmp = reinterpret_cast<double*>(b->reg64[free_reg(b)] + M.off64);
   if (b->precision == SBLI_FP32_DF) {
     SBLI_BTRY(launch_df_join(M.P, make_ref(b->params[member]), reinterpret_cast<const float*>(src), tmp, b->stream),
               "df_join");
@@ -579,7 +607,7 @@ int sbli_batch_kinetic_energy(sbli_batch* b, double* ke, double* enstrophy) {
   if (!ke || !enstrophy) return bfail(SBLI_EINVAL, "null output");
   for (int m = 0; m < b->count; ++m) {
     const MemberLayout& M = b->L.m[m];
-    const double* q = reinterpret_cast<double*>(b->reg64[b->state] + M.off64);
+    const double* q = reinterpret_cast<double*>(b->reg64[state_reg(b)] + M.off64);
     if (b->precision == SBLI_FP32_DF) {  // join into the register free at a step boundary
       double* tmp = reinterpret_cast<double*>(b->reg64[1 - b->state] + M.off64);
       SBLI_BTRY(launch_df_join(M.P, RefState{0.0, 0.0}, reinterpret_cast<const float*>(q), tmp, b->stream),
@@ -636,14 +664,16 @@ int sbli_batch_autotune(sbli_batch* b, int reps, int* z_queue, float* best_stage
     cudaEventDestroy(e0);
     return bcuda(ce, "cudaEventCreate");
   }
-  // time one schedule: one untimed and `reps` timed stage-0 launches, which
-  // read the state and write only the accumulator and stage registers
+  // time one schedule: one untimed and `reps` timed stage-0 launches with
+  // dt = 0, which write an accumulator equal to the state (acc + 0 * R; the
+  // double-float members update theirs in place) and a stage field into a
+  // free register
   cudaError_t err = cudaSuccess;
   auto time_schedule = [&](int zq, const std::vector<int>& zc) -> float {
     if (err == cudaSuccess) err = apply_schedule(b, zq, zc);
-    if (err == cudaSuccess) err = enqueue_batch_stage(b, 0, b->state, 1e-6, nullptr, b->stream);
+    if (err == cudaSuccess) err = enqueue_batch_stage(b, 0, b->state, 0.0, nullptr, b->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = enqueue_batch_stage(b, 0, b->state, 1e-6, nullptr, b->stream);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r) err = enqueue_batch_stage(b, 0, b->state, 0.0, nullptr, b->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 1e30f;

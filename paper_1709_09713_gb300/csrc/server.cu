@@ -182,12 +182,23 @@ StageArgs req_stage(const sbli_server* s, const Req& q, int k, bool* in64) {
   a.amb_dt32 = (float)a.amb_dt;
   a.df_normalize = (k == 2);
   const int st = q.state;
-  if (req_f64_registers(q.r.precision)) {
+  if (q.r.precision == SBLI_DF64) {
+    // accumulator in place in register 0; stage fields of (hi, lo) pairs
+    // alternate between registers st (the pair copy of Q^n) and 3 - st
+    double* S = r64(s, q, 0);
+    double* Pa = r64(s, q, st);
+    double* Pb = r64(s, q, 3 - st);
+    *in64 = false;
+    a.acc_in = S;
+    a.acc_out = S;
+    if (k == 0) { a.q_in = Pa; a.q_out = Pb; }
+    else if (k == 1) { a.q_in = Pb; a.q_out = Pa; }
+    else { a.q_in = Pa; a.q_out = Pb; }  // a_3 = b_3: the pair copy of Q^{n+1}
+  } else if (req_f64_registers(q.r.precision)) {
     double* S = r64(s, q, st);
     double* A = r64(s, q, (st + 1) % 3);
     double* B = r64(s, q, (st + 2) % 3);
-    // double-float arithmetic: stages 1 and 2 read stage fields of (hi, lo) pairs
-    *in64 = !(q.r.precision == SBLI_DF64 && k > 0);
+    *in64 = true;
     if (k == 0) { a.q_in = S; a.acc_in = S; a.acc_out = A; a.q_out = B; }
     else if (k == 1) { a.q_in = B; a.acc_in = A; a.acc_out = A; a.q_out = S; }
     else { a.q_in = S; a.acc_in = A; a.acc_out = A; a.q_out = nullptr; }
@@ -264,12 +275,23 @@ int valid_request(const sbli_request* r) {
 
 int lane_of(int precision) { return req_f64_registers(precision) ? 0 : 1; }
 
+// Register rotation of a request (as for single grids): double-float requests
+// keep the binary64 state in register 0 and the pair copy of the state in
+// register `state` (1 or 2); the others keep the state in register `state`.
+int req_initial_state(int precision) { return precision == SBLI_DF64 ? 1 : 0; }
+int req_next_state(int precision, int st) {
+  if (precision == SBLI_DF64) return 3 - st;
+  return req_f64_registers(precision) ? (st + 1) % 3 : 1 - st;
+}
+int req_state_reg(const Req& q) { return q.r.precision == SBLI_DF64 ? 0 : q.state; }
+int req_free_reg(const Req& q) { return q.r.precision == SBLI_DF64 ? 3 - q.state : (q.state + 1) % 2; }
+
 // Final diagnostics and copy-out of a finished request; frees its block.
 int retire(sbli_server* s, Req& q) {
   cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
   const Geom g{q.r.n0, q.r.n1, q.r.n2, q.P};
   const int n[3] = {q.r.n0, q.r.n1, q.r.n2};
-  const double* state = r64(s, q, q.state);
+  const double* state = r64(s, q, req_state_reg(q));
   if (q.r.precision == SBLI_FP32_DF) {
     // join the double-float state (deviation form) into the other register
     double* joined = r64(s, q, 1 - q.state);
@@ -281,7 +303,7 @@ int retire(sbli_server* s, Req& q) {
   double h[2];
   SBLI_STRY(cudaMemcpyAsync(h, s->ke_dev, sizeof h, cudaMemcpyDeviceToHost, st), "D2H");
   if (q.r.result) {
-    double* tmp = r64(s, q, (q.state + 1) % 2);  // a register the finished state does not occupy
+    double* tmp = r64(s, q, req_free_reg(q));  // a register the finished state does not occupy
     if (q.r.precision == SBLI_FP32_DF) {
       SBLI_STRY(launch_df_join(q.P, make_ref(q.r.params), reinterpret_cast<const float*>(r64(s, q, q.state)), tmp, st),
                 "df_join");
@@ -402,7 +424,7 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     it = s->pending.erase(it);
     q.off = off;
     q.t_admit = s->now();
-    q.state = 0;
+    q.state = req_initial_state(q.r.precision);
     q.remaining = q.r.steps;
     cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
     const Geom qg{q.r.n0, q.r.n1, q.r.n2, q.P};
@@ -413,6 +435,9 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     } else {
       SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 0), st), "init_tgv");
       if (q.r.precision == SBLI_FP32) SBLI_STRY(launch_narrow(5 * q.P, r64(s, q, 0), r32(s, q, 0), st), "narrow");
+      if (q.r.precision == SBLI_DF64)
+        SBLI_STRY(launch_pair_split(5 * q.P, r64(s, q, 0), reinterpret_cast<float*>(r64(s, q, q.state)), st),
+                  "pair_split");
     }
     s->active.push_back(q);
   }
@@ -470,7 +495,7 @@ int sbli_server_tick(sbli_server* s, int* completed) {
           if (has[SBLI_FP32_DF])
             SBLI_STRY(launch_group<float>(s, k, SBLI_FP32_DF, run, L.st, s->grid32), "fp32 double-float stage");
         }
-        for (Req* q : run) q->state = req_f64_registers(q->r.precision) ? (q->state + 1) % 3 : 1 - q->state;
+        for (Req* q : run) q->state = req_next_state(q->r.precision, q->state);
       }
       SBLI_STRY(cudaEventRecord(L.ev1, L.st), "cudaEventRecord");
       for (Req* q : run) q->remaining -= K;

@@ -370,6 +370,27 @@ def test_autotune_keeps_state_and_picks_a_valid_config(S):
         g.set_config(8, 8, 1, 2)  # ... with the shared-memory ring
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_autotune_leaves_every_register_of_the_state(S, precision):
+    """The autotuner's trial stages leave the state bitwise as it was, and
+    with it every copy the next step reads (the binary32 copy, the (hi, lo)
+    pair copy of a double-float grid whose state is updated in place): the
+    steps after autotuning equal those of a grid that was never tuned."""
+    n, dt = (40, 24, 20), 1e-3
+    g = S.Grid(n, precision, S.SBLI_FUSED)
+    g.init_tgv()
+    g.step_n(2, dt)
+    before = g.get_state()
+    cfg = g.autotune(reps=1)[:4]
+    assert torch.equal(g.get_state(), before)
+    g.step_n(3, dt)
+    ref = S.Grid(n, precision, S.SBLI_FUSED)
+    ref.set_config(*cfg)
+    ref.init_tgv()
+    ref.step_n(5, dt)
+    assert torch.equal(g.get_state(), ref.get_state())
+
+
 def test_fp32_kinetic_energy_history_512_subsample_bound(S, orc):
     """FP32 path against the binary64 GPU path at a larger grid (64^3, 20
     steps): fields within 1e-5, KE history within 1e-6."""
