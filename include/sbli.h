@@ -231,7 +231,9 @@ SBLI_API int sbli_set_config(sbli_grid* g, int tile_y, int planes_per_cta, int z
 /* Autotuner: times candidate configurations (each allowed tile height, z
  * queue and columns per thread with the six planes-per-CTA values a
  * wave-balance model ranks best) on this grid with `reps` timed stage-0 launches each,
- * which read the state and write only the scratch registers, keeps the
+ * at dt = 0 (the accumulator they write equals the state they read, so a
+ * double-float grid's state, updated in place, keeps its value; the stage
+ * field goes to a free register), keeps the
  * fastest and returns it.  The state is not changed.  Synchronises the grid's
  * stream.  Fused variant only. */
 SBLI_API int sbli_autotune(sbli_grid* g, int reps, int* tile_y, int* planes_per_cta, int* z_queue,
@@ -268,9 +270,10 @@ SBLI_API int sbli_batch_work_items(const sbli_batch* b, long long* items);
  * be NULL in both calls (keep, or do not return, the per-member values). */
 SBLI_API int sbli_batch_get_schedule(const sbli_batch* b, int* z_queue, int* planes_per_item);
 SBLI_API int sbli_batch_set_schedule(sbli_batch* b, int z_queue, const int* planes_per_item);
-/* Autotuner of the schedule: times non-destructive stage-0 launches (reps
- * each; they read the state and write only the accumulator and stage
- * registers) of every z_queue mode with one planes-per-item value for all
+/* Autotuner of the schedule: times stage-0 launches with dt = 0 (reps each;
+ * the accumulator they write equals the state they read, so a state updated
+ * in place keeps its value, and the stage field goes to a free register) of
+ * every z_queue mode with one planes-per-item value for all
  * members (8, 16, 32, 64, 128, whole member), then refines the planes per
  * item of each size class (members with the same n2) in turn, and keeps the
  * fastest schedule.  The state is not changed.  Synchronises the batch's

@@ -977,12 +977,16 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           for (int f = 0; f < NF; ++f) a.r_out[(long long)f * a.g.P + o] = double(lane(R[f], j));
         } else if constexpr (DF) {
           // binary32 stage, double-float accumulator (hi + lo, binary32
-          // each): acc' = acc + (b dt R) by an error-free two-sum of hi and
-          // the increment, the error folded into lo; Q_{k+1} = hi' + (lo' +
-          // (a - b) dt R).  The pair (hi', lo') represents acc' whether or not
-          // it is normalised; the last stage of a step renormalises it, so
-          // that the state's hi fields are its binary32 rounding (the next
-          // step's stage-0 input), the others leave it as it is.
+          // each): acc' = acc + (b dt R) by Dekker's Fast2Sum of hi and the
+          // increment x = fl(b dt R), the error folded into lo; Q_{k+1} = hi'
+          // + (lo' + (a - b) dt R).  Fast2Sum is exact when |hi| >= |x|;
+          // otherwise (hi crossing zero) the pair misses hi + x by at most
+          // about half an ulp of x, the size of the rounding x already
+          // carries, so the accumulator keeps its precision where it
+          // matters.  The pair (hi', lo') represents acc' whether or not it
+          // is normalised; the last stage of a step renormalises it, so that
+          // the state's hi fields are its binary32 rounding (the next step's
+          // stage-0 input), the others leave it as it is.
           const float bdt = a.b_dt32, ambdt = a.amb_dt32;
           float hi3[NF], lo3[NF], rr[NF];
 #pragma unroll
@@ -990,8 +994,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             rr[f] = float(lane(R[f], j));
             const float x = bdt * rr[f];
             const float s = __fadd_rn(dhi[f][j], x);
-            const float bb = __fsub_rn(s, dhi[f][j]);
-            const float err = __fadd_rn(__fsub_rn(dhi[f][j], __fsub_rn(s, bb)), __fsub_rn(x, bb));
+            const float err = __fsub_rn(x, __fsub_rn(s, dhi[f][j]));
             hi3[f] = s;
             lo3[f] = __fadd_rn(dlo[f][j], err);
           }
