@@ -987,30 +987,55 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           // is normalised; the last stage of a step renormalises it, so that
           // the state's hi fields are its binary32 rounding (the next step's
           // stage-0 input), the others leave it as it is.
+          // Fields are updated two at a time with packed two-lane
+          // instructions (the same correctly rounded binary32 operations as
+          // one field at a time), the last field alone.
           const float bdt = a.b_dt32, ambdt = a.amb_dt32;
           float hi3[NF], lo3[NF], rr[NF];
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            rr[f] = float(lane(R[f], j));
-            const float x = bdt * rr[f];
-            const float s = __fadd_rn(dhi[f][j], x);
-            const float err = __fsub_rn(x, __fsub_rn(s, dhi[f][j]));
-            hi3[f] = s;
-            lo3[f] = __fadd_rn(dlo[f][j], err);
-          }
-          if (a.df_normalize) {
+          for (int f = 0; f < NF; ++f) rr[f] = float(lane(R[f], j));
+          const float2 bdt2 = make_float2(bdt, bdt), ambdt2 = make_float2(ambdt, ambdt);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-              const float h = __fadd_rn(hi3[f], lo3[f]);
-              lo3[f] = __fsub_rn(lo3[f], __fsub_rn(h, hi3[f]));
+          for (int f = 0; f < NF; f += 2) {
+            if (f + 1 < NF) {
+              const float2 r2 = make_float2(rr[f], rr[f + 1]);
+              const float2 h2 = make_float2(dhi[f][j], dhi[f + 1][j]);
+              const float2 x2 = __fmul2_rn(bdt2, r2);
+              const float2 s2 = __fadd2_rn(h2, x2);
+              const float2 d2 = __fadd2_rn(s2, make_float2(-h2.x, -h2.y));
+              const float2 e2 = __fadd2_rn(x2, make_float2(-d2.x, -d2.y));
+              float2 l2 = __fadd2_rn(make_float2(dlo[f][j], dlo[f + 1][j]), e2);
+              float2 hn = s2;
+              if (a.df_normalize) {
+                hn = __fadd2_rn(s2, l2);
+                const float2 g2 = __fadd2_rn(hn, make_float2(-s2.x, -s2.y));
+                l2 = __fadd2_rn(l2, make_float2(-g2.x, -g2.y));
+              }
+              const float2 q2 = __fadd2_rn(hn, __ffma2_rn(ambdt2, r2, l2));
+              hi3[f] = hn.x;
+              hi3[f + 1] = hn.y;
+              lo3[f] = l2.x;
+              lo3[f + 1] = l2.y;
+              qo[f] = TOUT(q2.x);
+              qo[f + 1] = TOUT(q2.y);
+            } else {
+              const float x = bdt * rr[f];
+              const float s = __fadd_rn(dhi[f][j], x);
+              const float err = __fsub_rn(x, __fsub_rn(s, dhi[f][j]));
+              float h = s, l = __fadd_rn(dlo[f][j], err);
+              if (a.df_normalize) {
+                h = __fadd_rn(s, l);
+                l = __fsub_rn(l, __fsub_rn(h, s));
+              }
               hi3[f] = h;
+              lo3[f] = l;
+              qo[f] = TOUT(h + fmaf(ambdt, rr[f], l));
             }
           }
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             a.dacc_out[(long long)f * a.g.P + o] = hi3[f];
             a.dacc_out[(long long)(NF + f) * a.g.P + o] = lo3[f];
-            qo[f] = TOUT(hi3[f] + fmaf(ambdt, rr[f], lo3[f]));
           }
         } else if constexpr (is_f64_class<T>()) {
           // binary64 (or double-float) stage: acc + b dt R and acc + a dt R,
