@@ -276,7 +276,9 @@ SBLI_API int sbli_batch_set_schedule(sbli_batch* b, int z_queue, const int* plan
  * every z_queue mode with one planes-per-item value for all
  * members (8, 16, 32, 64, 128, whole member), then refines the planes per
  * item of each size class (members with the same n2) in turn, and keeps the
- * fastest schedule.  The state is not changed.  Synchronises the batch's
+ * fastest schedule (if a trial launch fails, the schedule in place before
+ * the call is restored and SBLI_ECUDA returned).  The state is not
+ * changed.  Synchronises the batch's
  * stream.  *z_queue and *best_stage_ms (may be NULL) return the choice and
  * its stage time; sbli_batch_get_schedule returns the planes per item. */
 SBLI_API int sbli_batch_autotune(sbli_batch* b, int reps, int* z_queue, float* best_stage_ms);
@@ -352,7 +354,10 @@ SBLI_API int sbli_server_submit(sbli_server* s, const sbli_request* r, long long
  * retire its finished requests and launch its next batch (a lane still
  * running is left alone).  If neither lane could make progress, waits up to
  * about 2 ms for one to finish.  Returns without synchronising a running
- * lane; *completed = requests retired by this tick. */
+ * lane; *completed = requests retired by this tick.  SBLI_ECUDA if a launch
+ * or copy fails: a request whose initial field could not be launched goes
+ * back to the head of the queue with its block released; a request whose
+ * retirement failed stays active and is retried by the next tick. */
 SBLI_API int sbli_server_tick(sbli_server* s, int* completed);
 /* Move up to max retired requests' results into out; *n = how many. */
 SBLI_API int sbli_server_poll(sbli_server* s, sbli_result* out, int max, int* n);

@@ -690,6 +690,8 @@ int sbli_batch_autotune(sbli_batch* b, int reps, int* z_queue, float* best_stage
   int best_zq = b->zq;
   std::vector<int> best_zc(b->count);
   for (int m = 0; m < b->count; ++m) best_zc[m] = b->L.m[m].zc;
+  const int start_zq = best_zq;
+  const std::vector<int> start_zc = best_zc;  // restored if a trial launch fails
   float best = time_schedule(best_zq, best_zc);
   for (int zq = 0; zq <= 1; ++zq)
     for (int Z : Zs) {
@@ -720,7 +722,10 @@ int sbli_batch_autotune(sbli_batch* b, int reps, int* z_queue, float* best_stage
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (err != cudaSuccess) return bcuda(err, "autotune launch");
+  if (err != cudaSuccess) {
+    apply_schedule(b, start_zq, start_zc);
+    return bcuda(err, "autotune launch");
+  }
   SBLI_BTRY(apply_schedule(b, best_zq, best_zc), "schedule");
   if (z_queue) *z_queue = best_zq;
   if (best_stage_ms) *best_stage_ms = best;

@@ -286,6 +286,25 @@ int req_next_state(int precision, int st) {
 int req_state_reg(const Req& q) { return q.r.precision == SBLI_DF64 ? 0 : q.state; }
 int req_free_reg(const Req& q) { return q.r.precision == SBLI_DF64 ? 3 - q.state : (q.state + 1) % 2; }
 
+// Taylor-Green initial field of a newly admitted request in its registers,
+// on its lane's stream.
+int init_request(sbli_server* s, const Req& q) {
+  cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
+  const Geom qg{q.r.n0, q.r.n1, q.r.n2, q.P};
+  if (q.r.precision == SBLI_FP32_DF) {  // binary64 deviation field, then split into hi/lo
+    SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 1), st), "init_tgv");
+    SBLI_STRY(launch_df_split(q.P, RefState{0.0, 0.0}, r64(s, q, 1), reinterpret_cast<float*>(r64(s, q, 0)), st),
+              "df_split");
+  } else {
+    SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 0), st), "init_tgv");
+    if (q.r.precision == SBLI_FP32) SBLI_STRY(launch_narrow(5 * q.P, r64(s, q, 0), r32(s, q, 0), st), "narrow");
+    if (q.r.precision == SBLI_DF64)
+      SBLI_STRY(launch_pair_split(5 * q.P, r64(s, q, 0), reinterpret_cast<float*>(r64(s, q, q.state)), st),
+                "pair_split");
+  }
+  return SBLI_OK;
+}
+
 // Final diagnostics and copy-out of a finished request; frees its block.
 int retire(sbli_server* s, Req& q) {
   cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
@@ -426,18 +445,10 @@ int sbli_server_tick(sbli_server* s, int* completed) {
     q.t_admit = s->now();
     q.state = req_initial_state(q.r.precision);
     q.remaining = q.r.steps;
-    cudaStream_t st = s->lane[lane_of(q.r.precision)].st;
-    const Geom qg{q.r.n0, q.r.n1, q.r.n2, q.P};
-    if (q.r.precision == SBLI_FP32_DF) {  // binary64 deviation field, then split into hi/lo
-      SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 1), st), "init_tgv");
-      SBLI_STRY(launch_df_split(q.P, RefState{0.0, 0.0}, r64(s, q, 1), reinterpret_cast<float*>(r64(s, q, 0)), st),
-                "df_split");
-    } else {
-      SBLI_STRY(launch_init_tgv(qg, q.r.params, q.r.amplitude, r64(s, q, 0), st), "init_tgv");
-      if (q.r.precision == SBLI_FP32) SBLI_STRY(launch_narrow(5 * q.P, r64(s, q, 0), r32(s, q, 0), st), "narrow");
-      if (q.r.precision == SBLI_DF64)
-        SBLI_STRY(launch_pair_split(5 * q.P, r64(s, q, 0), reinterpret_cast<float*>(r64(s, q, q.state)), st),
-                  "pair_split");
+    if (int rc = init_request(s, q)) {  // back to the head of the queue, its block free again
+      s->alloc->release(q.off, q.bytes);
+      s->pending.push_front(q);
+      return rc;
     }
     s->active.push_back(q);
   }
