@@ -30,8 +30,9 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, TY, ZT>& sm = *reinterpret_cast<FusedSmem<T, TY, ZT>*>(smem_raw);
   constexpr int NCOL = tmem_columns<TY, T>();
-  uint32_t tbase = 0;
-  if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
+  constexpr int NCOL2 = tmem_columns2<TY, T>();
+  uint32_t tbase = 0, tbase2 = 0;
+  if (ZT) tmem_acquire<NCOL, NCOL2>(sm.tmem_base, tbase, tbase2);
   for (long long item = blockIdx.x; item < p.total_items; item += gridDim.x) {
     // member owning this item (binary search over item_begin)
     int lo = 0, hi = p.count - 1;
@@ -49,10 +50,10 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
     const int zbeg = chunk * a.zc;
     double ke = 0.0, ens = 0.0;
     fused_march<T, TIN, TOUT, TY, false, WITH_KE, DF, ZT>(a, p.c[lo], bx, by, zbeg, zbeg + a.zc, sm, ke, ens,
-                                                            tbase);
+                                                            tbase, tbase2);
     if (WITH_KE) block_reduce_pair<TX * TY>(sm.red, ke, ens, p.ke_items + 2 * item);
   }
-  if (ZT) tmem_release<NCOL>(tbase);
+  if (ZT) tmem_release<NCOL, NCOL2>(tbase, tbase2);
 }
 
 // Per member: fixed-order sum of its items' partials, scaled by 1/P.

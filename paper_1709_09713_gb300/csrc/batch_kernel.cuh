@@ -35,9 +35,9 @@ cudaError_t launch_batch_t(const BatchParams<T>& p, bool in64, int grid, cudaStr
 inline int batch_default_zq(int precision) { return precision == SBLI_FP32 || precision == SBLI_FP32_DF ? 1 : 0; }
 
 // Resident CTAs per SM of the multi-member launch: binary32 members run the
-// TMEM-queue kernel (64 KiB shared, 80 registers: 3 per SM) or the shared
-// ring (97.5 KiB: 2 per SM); binary64 and double-float-arithmetic members
-// the 194.5 KiB shared ring or the 127 KiB TMEM-queue kernel (1 per SM).
+// TMEM-queue kernel (59 KiB shared, 80 registers: 3 per SM) or the shared
+// ring (113 KiB: 2 per SM); binary64 and double-float-arithmetic members
+// the 194.5 KiB shared ring or the 124 KiB TMEM-queue kernel (1 per SM).
 inline int batch_ctas_per_sm(int precision, int zq) {
   if (precision == SBLI_FP32 || precision == SBLI_FP32_DF) return zq ? 3 : 2;
   return 1;

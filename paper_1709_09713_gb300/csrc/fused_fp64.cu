@@ -1,6 +1,6 @@
 // fused_fp64.cu -- binary64 instantiations of the fused stage kernel
 // (32 x 8 tiles: 80-byte records fill 194.5 KiB of shared memory per CTA with
-// the five-plane ring, 127 KiB with the x2 queue in TMEM).
+// the five-plane ring, 124 KiB with the x2 queue in TMEM).
 #include "fused_stage.cuh"
 
 namespace sbli {

@@ -24,24 +24,34 @@
 //     one at a time (axis_terms_stream; the double-float type keeps the
 //     difference-first form, axis_terms);
 //   * ZT (the z queue): each thread keeps its own column's records of the
-//     five ring planes, and their D1_x u0 / D1_y u1, in tensor memory (TMEM),
-//     so the x2 derivatives read TMEM and shared memory keeps full records
-//     only for the entering, middle and centre planes, plus u_2 of the five
-//     planes for D1_z u_2 on the halo: binary32 64 KiB per 32 x 8 CTA, three
-//     CTAs per SM (binary64 and double-float records take two TMEM columns
-//     per value: 127 KiB, one CTA).  32 x 16 binary32 tiles (one CTA per SM)
-//     keep a fourth full-record plane (the one that was the centre one plane
-//     earlier): the next entering plane then overwrites a slot nobody reads
-//     any more, so the barrier that ends each plane is not needed (two
-//     barriers per plane instead of three);
+//     five ring planes, and their in-plane gradients, in tensor memory
+//     (TMEM), so the x2 derivatives read TMEM and shared memory keeps full
+//     records only for the entering, middle and centre planes: binary32 59 KiB
+//     per 32 x 8 CTA, three CTAs per SM (binary64 and double-float records
+//     take two TMEM columns per value and keep u_2 of the five planes for
+//     D1_z u_2 on the halo: 124 KiB, one CTA).  32 x 16 binary32 tiles (one
+//     CTA per SM) keep a fourth full-record plane (the one that was the
+//     centre one plane earlier): the next entering plane then overwrites a
+//     slot nobody reads any more, so the barrier that ends each plane is not
+//     needed;
 //   * the arithmetic type T is double, float, dfloat (double-float, binary64
 //     storage) or f32x2 (two columns per thread in packed FP32x2 instructions);
-//   * the mixed second derivatives of the stress divergence use, for each i,
-//       sum_{j != i} d2 u_j/dx_i dx_j = D1_i( s_i ),  s_i = sum_{j != i} D1_j u_j,
-//     (linearity of D1_i; the D1_a o D1_b reading of the mixed term), so
-//     only the three diagonal gradients D1_j u_j are needed around a point:
-//     D1_x u0 and D1_y u1 are kept per plane, D1_z u2 is formed on the
-//     centre plane's tile and halo.
+//   * the mixed second derivatives of the stress divergence (the D1_a o D1_b
+//     reading of the mixed term), for each i sum_{j != i} d2 u_j/dx_i dx_j:
+//     - binary64 and double-float, by linearity of D1_i,
+//         = D1_i( s_i ),  s_i = sum_{j != i} D1_j u_j,
+//       so only the three diagonal gradients D1_j u_j are needed around a
+//       point: D1_x u0 and D1_y u1 are kept per plane, D1_z u2 is formed on
+//       the centre plane's tile and halo (a third barrier per plane);
+//     - binary32, with every x2 derivative applied last (D1_a and D1_b
+//       commute on the periodic grid):
+//         i = 0:  D1_x(D1_y u1) + D1_z(D1_x u2)
+//         i = 1:  D1_y(D1_x u0) + D1_z(D1_y u2)
+//         i = 2:  D1_z(D1_x u0 + D1_y u1)
+//       so the halo helpers D1_y u1 and D1_x u0 are in-plane, formed as a
+//       plane enters (three planes of helper buffers), and the x2 parts come
+//       from the thread's own column (D1_x u2, D1_y u2 kept per plane in a
+//       second TMEM window): no u_2 on the halo and two barriers per plane.
 //
 // Variables are stored as deviations from the reference state
 // (rho' = rho - 1, rho u_i, (rho E)' = rho E - p_ref/(gamma-1)), which keeps
@@ -80,19 +90,33 @@ template <int TY, bool ZT>
 constexpr int full_slots() {
   return ZT ? (TY >= 16 ? 4 : 3) : NSLOT;
 }
+// Binary32 arithmetic types group the mixed second derivatives so that the
+// x2 derivative is applied last (see fused_march): their helpers are
+// in-plane and formed as each plane enters.
+template <typename T>
+constexpr bool mixz() {
+  return std::is_same<T, float>::value || std::is_same<T, f32x2>::value;
+}
 template <typename T, int TY, bool ZT = false>
 struct FusedSmem {
   static constexpr int SY = TY + 2 * HALO;
   static constexpr int NFULL = full_slots<TY, ZT>();
+  static constexpr bool MIXZ = mixz<T>();
+  static constexpr bool U2 = ZT && !MIXZ;      // u_2 ring (binary64 / double-float TMEM queue)
+  static constexpr int NDV = MIXZ ? 4 : 2;     // per-plane gradients in the shared ring
+  static constexpr int NSB = MIXZ ? 3 : 1;     // planes of helper buffers
   T ring[NFULL][SY][SX][NV];  // rho', m_i, E', u_i, p', T' per haloed point
-  union {
-    T u2ring[NSLOT][SY][SX];    // ZT: u_2 per haloed point of the five ring planes
-    T dring[NSLOT][2][TY][TX];  // otherwise: D1_x u0 and D1_y u1 per plane (tile only)
-  };
-  T s0buf[TY][SX];            // s_0 = D1_y u1 + D1_z u2, centre plane, x0-haloed rows
-  T s1buf[SY][TX];            // s_1 = D1_x u0 + D1_z u2, centre plane, x1-haloed columns
+  T u2ring[U2 ? NSLOT : 1][U2 ? SY : 1][U2 ? SX : 1];  // u_2 per haloed point of the five ring planes
+  // without the TMEM queue: D1_x u0, D1_y u1 (and, binary32, D1_x u2, D1_y u2)
+  // per plane (tile only)
+  T dring[ZT ? 1 : NSLOT][ZT ? 1 : NDV][ZT ? 1 : TY][ZT ? 1 : TX];
+  // binary64 / double-float: s_0 = D1_y u1 + D1_z u2 and s_1 = D1_x u0 + D1_z u2
+  // on the centre plane; binary32: D1_y u1 and D1_x u0 of the last three
+  // planes to enter (x0-haloed rows, x1-haloed columns)
+  T s0buf[NSB][TY][SX];
+  T s1buf[NSB][SY][TX];
   double red[2][32];          // block reduction of (ke, enstrophy)
-  uint32_t tmem_base;         // TMEM allocation (z queue variant)
+  uint32_t tmem_base[2];      // TMEM allocations (z queue variant)
 };
 
 // 1/rho for the primitives (Eqs. 4-5): correctly rounded in binary64 and
@@ -200,6 +224,17 @@ struct TmLayout {
 template <int NW, typename T = float>
 constexpr int tmem_columns() {
   constexpr int need = TmLayout<T>::COLS * ((NW + 3) / 4);
+  int c = 32;
+  while (c < need) c *= 2;
+  return c;
+}
+// The binary32 queue's second window (a separate allocation): the pair
+// (D1_x u2, D1_y u2) of slot s in columns 2s, 2s + 1 of a 16-column window.
+constexpr int TM_XCOLS = 16;
+template <int NW, typename T = float>
+constexpr int tmem_columns2() {
+  if (!mixz<T>()) return 0;
+  constexpr int need = TM_XCOLS * ((NW + 3) / 4);
   int c = 32;
   while (c < need) c *= 2;
   return c;
@@ -355,31 +390,41 @@ __device__ __forceinline__ void tmem_load_diag(uint32_t, int, f32x2&, f32x2&) {}
 __device__ __forceinline__ void tmem_load_rec(uint32_t, int, f32x2 (&)[NV]) {}
 __device__ __forceinline__ void tmem_store_rec(uint32_t, int, const f32x2 (&)[NV]) {}
 
-// Allocate / release the CTA's TMEM columns (warp 0), publishing the base
-// address through shared memory.  The CTAs that shared memory lets share an
-// SM never ask for more than the 512 columns available (binary32 32 x 8:
-// 3 x 128; 32 x 16: 256; binary64 and double-float 32 x 8: 256, one CTA),
+// Allocate / release the CTA's TMEM columns (warp 0): NCOL for the queue
+// and, binary32, NCOL2 for its second window, publishing the base addresses
+// through shared memory.  The CTAs that shared memory lets share an SM never
+// ask for more than the 512 columns available (binary32 32 x 8: 3 x (128 +
+// 32); 32 x 16: 256 + 64; binary64 and double-float 32 x 8: 256, one CTA),
 // so the allocation never waits.
-template <int NCOL>
-__device__ __forceinline__ uint32_t tmem_acquire(uint32_t* smem_slot) {
+template <int NCOL, int NCOL2 = 0>
+__device__ __forceinline__ void tmem_acquire(uint32_t (&smem_slot)[2], uint32_t& base, uint32_t& base2) {
   if ((threadIdx.x >> 5) == 0) {
-    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_slot);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&smem_slot[0]);
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(NCOL) : "memory");
+    if (NCOL2 > 0) {
+      const uint32_t dst2 = (uint32_t)__cvta_generic_to_shared(&smem_slot[1]);
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst2), "r"(NCOL2)
+                   : "memory");
+    }
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return *(volatile uint32_t*)smem_slot;
+  base = *(volatile uint32_t*)&smem_slot[0];
+  base2 = NCOL2 > 0 ? *(volatile uint32_t*)&smem_slot[1] : 0u;
 }
 
-template <int NCOL>
-__device__ __forceinline__ void tmem_release(uint32_t base) {
+template <int NCOL, int NCOL2 = 0>
+__device__ __forceinline__ void tmem_release(uint32_t base, uint32_t base2) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if ((threadIdx.x >> 5) == 0)
+  if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(NCOL) : "memory");
+    if (NCOL2 > 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base2), "r"(NCOL2) : "memory");
+  }
 }
 
 // This thread's TMEM window: lane quarter of its warp, column window warp / 4.
@@ -387,6 +432,30 @@ template <typename T>
 __device__ __forceinline__ uint32_t tmem_window(uint32_t base) {
   const uint32_t w = threadIdx.x >> 5;
   return base + (((w & 3u) * 32u) << 16) + (w >> 2) * (uint32_t)TmLayout<T>::COLS;
+}
+__device__ __forceinline__ uint32_t tmem_window2(uint32_t base2) {
+  const uint32_t w = threadIdx.x >> 5;
+  return base2 + (((w & 3u) * 32u) << 16) + (w >> 2) * (uint32_t)TM_XCOLS;
+}
+// the pair (D1_x u2, D1_y u2) of this thread's column in slot `slot` of the
+// second window
+__device__ __forceinline__ void tmem_store_xdiag(uint32_t win2, int slot, float d02, float d12) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(win2 + (uint32_t)(2 * slot)),
+      "r"(__float_as_uint(d02)), "r"(__float_as_uint(d12))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_load_xdiag(uint32_t win2, int slot, float& d02, float& d12) {
+  uint32_t a, b;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(a), "=r"(b)
+      : "r"(win2 + (uint32_t)(2 * slot))
+      : "memory");
+  d02 = __uint_as_float(a);
+  d12 = __uint_as_float(b);
 }
 
 // Stage input value in the arithmetic type (binary64 inputs to a binary32
@@ -521,11 +590,32 @@ __device__ __forceinline__ void axis_terms(const LD& ldrec, const SF& sfun, cons
 // operations than the difference-first form for hardware FMA types; the
 // double-float type keeps the difference-first form (its products cost more
 // than its sums).
-template <int A, typename T, typename LD, typename SF>
+// a + b, never contracted with the product that formed b (so its rounding
+// does not depend on how the compiler schedules that product)
+__device__ __forceinline__ float add_nc(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ f32x2 add_nc(f32x2 a, f32x2 b) { return a + b; }
+template <typename T>
+__device__ __forceinline__ T add_nc(T a, T b) {
+  return a + b;
+}
+
+// No x2-regrouped mixed terms (every axis but the binary32 x2 axis).
+struct NoXTerms {
+  template <typename T>
+  __device__ void operator()(int, T&, T&) const {}
+};
+
+// ZX (binary32, A = 2): the mixed derivatives that involve x2 are taken with
+// the x2 derivative last, D1_z(D1_x u2) and D1_z(D1_y u2) from xfun(k, ...)
+// (the neighbours' in-plane gradients of u2), added to G_0 and G_1; the
+// stream also forms D1_z u2 at the centre (g_22).
+template <int A, bool ZX = false, typename T, typename LD, typename SF, typename XF = NoXTerms>
 __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfun, const Coef<T>& c,
-                                                  const T (&uc)[3], Terms<T>& t) {
+                                                  const T (&uc)[3], Terms<T>& t, const XF& xfun = XF()) {
+  static_assert(!ZX || A == 2, "x2-last mixed terms belong to the x2 axis");
   const T c1 = c.c1[A], c2 = c.c2[A], e1 = c.e1[A], e2 = c.e2[A];
   const T ua = uc[A];
+  T gz0 = T(0), gz1 = T(0), g22 = T(0);  // ZX only
   T lAA = T(0);                       // sum_k e_k u_A,k: D2_A u_A without its centre term
   T gA = T(0);                        // sum_k c_k s_k = D1_A s_A
   T gI[3] = {T(0), T(0), T(0)};      // D1_A u_i, i != A
@@ -557,12 +647,24 @@ __device__ __forceinline__ void axis_terms_stream(const LD& ldrec, const SF& sfu
     lAA = mad(ed, r[V_U0 + A], lAA);  // shared by the Laplacian of u_A and G_A
     gA = mad(cd, sk, gA);
     t.lapT = mad(ed, r[V_T], t.lapT);
+    if constexpr (ZX) {
+      T x02, x12;
+      xfun(k, x02, x12);
+      gz0 = mad(cd, x02, gz0);
+      gz1 = mad(cd, x12, gz1);
+      g22 = add_nc(g22, x);  // x = cd u_2 (above): an add the compiler may not contract
+    }
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     if (i != A) t.g[i][A] = gI[i];
   t.lap[A] += lAA;
   t.G[A] = fma(c.e0[A], uc[A], lAA + gA);  // D2_A u_A + D1_A s_A (Eq. 7 on j = A, D1 o D1 otherwise)
+  if constexpr (ZX) {
+    t.G[0] = t.G[0] + gz0;
+    t.G[1] = t.G[1] + gz1;
+    t.g[2][2] = g22;
+  }
 }
 
 // Eqs. 1-3 at one point from the accumulated derivative terms and the
@@ -590,19 +692,21 @@ __device__ __forceinline__ void assemble_residual(const Terms<T>& t, T rho_p, co
   R[4] = mad(c.kappa, lapT, mad(c.inv_re, uvisc + diss, mad(-c.H0, div, T(-0.5) * mad(Ec, div, t.rE))));
 }
 
-template <int A, typename T, typename LD, typename SF>
+template <int A, bool ZX = false, typename T, typename LD, typename SF, typename XF = NoXTerms>
 __device__ __forceinline__ void axis_terms_any(const LD& ldrec, const SF& sfun, const Coef<T>& c, const T (&uc)[3],
-                                               Terms<T>& t) {
-  if constexpr (std::is_same<T, dfloat>::value)
+                                               Terms<T>& t, const XF& xfun = XF()) {
+  if constexpr (std::is_same<T, dfloat>::value) {
+    static_assert(!ZX, "double-float keeps the s_i helpers");
     axis_terms<A>(ldrec, sfun, c, uc, t);
-  else
-    axis_terms_stream<A>(ldrec, sfun, c, uc, t);
+  } else {
+    axis_terms_stream<A, ZX>(ldrec, sfun, c, uc, t, xfun);
+  }
 }
 
 // TIN: type of the stage input in HBM; TOUT: type of the stage output.
 // CTAs per SM the launch bounds plan for: shared memory allows two 32 x 8
-// binary32 CTAs per SM with the 5-slot ring (97.5 KiB each) and three with
-// the TMEM queue and 3-slot ring (64 KiB each, 80 registers); binary64 and
+// binary32 CTAs per SM with the 5-slot ring (113 KiB each) and three with
+// the TMEM queue and 3-slot ring (59 KiB each, 80 registers); binary64 and
 // double-float (194.5 KiB) and 32 x 16 tiles take one.
 template <typename T, int TY, bool ZT = false>
 constexpr int fused_min_blocks() {
@@ -623,8 +727,9 @@ template <typename T, typename TIN, typename TOUT, int TY, bool RHS_ONLY, bool W
           bool ZT = false>
 __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c, int bx, int by, int zbeg, int zend_req,
                                             FusedSmem<T, TY, ZT>& sm, double& ke_acc, double& ens_acc,
-                                            uint32_t tmem_base = 0) {
+                                            uint32_t tmem_base = 0, uint32_t tmem_base2 = 0) {
   using S = FusedSmem<T, TY, ZT>;
+  constexpr bool MIXZ = S::MIXZ;
   constexpr int SY = S::SY;
   constexpr int NT = TX * TY;
   constexpr int PTS = SX * SY;
@@ -698,6 +803,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   // the window address is warp-uniform; broadcasting lane 0's copy lets the
   // compiler keep it in a uniform register for the tcgen05 operands
   const uint32_t twin = ZT ? __shfl_sync(0xffffffffu, tmem_window<T>(tmem_base), 0) : 0u;
+  const uint32_t twin2 = (ZT && MIXZ) ? __shfl_sync(0xffffffffu, tmem_window2(tmem_base2), 0) : 0u;
   T d22 = T(0);
   T g00c = T(0), g11c = T(0);  // D1_x u0, D1_y u1 at the centre point
 
@@ -739,6 +845,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
   int rf[ZT ? NFULL : 1];
 #pragma unroll
   for (int k = 0; k < (ZT ? NFULL : 1); ++k) rf[k] = (k + 1) % (ZT ? NFULL : 1);
+  // binary32 helper-buffer slots of planes e-2, e-1, e
+  int rb[3] = {1, 2, 0};
 
   TIN pf[LPT][NF][PP];
   int zl = wrapi(zbeg - HALO, n2);  // next plane to load (periodic), advanced one plane per load
@@ -777,6 +885,12 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       rf[NFULL - 1] = t0;
     }
     const int fe = ZT ? rf[ZT ? NFULL - 1 : 0] : se;  // full-record slot of the entering plane
+    if constexpr (MIXZ) {
+      const int t0 = rb[0];
+      rb[0] = rb[1];
+      rb[1] = rb[2];
+      rb[2] = t0;
+    }
     {
       T* ring = &sm.ring[fe][0][0][0];
 #pragma unroll
@@ -804,8 +918,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
           rec[V_P] = p2;
           rec[V_T] = T_p;
           store_rec(ring + ld_s[l] * NV, rec);
+          if constexpr (S::U2) (&sm.u2ring[se][0][0])[ld_s[l]] = u2;
           if constexpr (ZT) {
-            (&sm.u2ring[se][0][0])[ld_s[l]] = u2;
             if (l == 0) tmem_store_rec(twin, se, rec);  // l == 0: every thread
           }
         }
@@ -828,6 +942,36 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       } else {
         sm.dring[se][0][ty][tx] = d00;
         sm.dring[se][1][ty][tx] = d11;
+      }
+      if constexpr (MIXZ) {
+        // binary32: the in-plane gradients of u2 (for D1_z of them at the
+        // centre, from this thread's own column) and the helpers D1_y u1 on
+        // the x0-haloed rows and D1_x u0 on the x1-haloed columns of the
+        // entering plane, read when it becomes the centre
+        const T d02 = mad(c.c1[0], R[sy][sx + 1][V_U2] - R[sy][sx - 1][V_U2],
+                          -c.c2[0] * (R[sy][sx + 2][V_U2] - R[sy][sx - 2][V_U2]));
+        const T d12 = mad(c.c1[1], R[sy + 1][sx][V_U2] - R[sy - 1][sx][V_U2],
+                          -c.c2[1] * (R[sy + 2][sx][V_U2] - R[sy - 2][sx][V_U2]));
+        if constexpr (ZT) {
+          tmem_store_xdiag(twin2, se, d02, d12);
+        } else {
+          sm.dring[se][2][ty][tx] = d02;
+          sm.dring[se][3][ty][tx] = d12;
+        }
+        const int sbe = rb[2];
+        sm.s0buf[sbe][ty][sx] = d11;
+        sm.s1buf[sbe][sy][tx] = d00;
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+          const int hy = hxy[j] >> 8, hx = hxy[j] & 0xFF;
+          if (hk[j] == 1) {
+            (&sm.s0buf[sbe][0][0])[hdst[j]] = mad(c.c1[1], R[hy + 1][hx][V_U1] - R[hy - 1][hx][V_U1],
+                                                  -c.c2[1] * (R[hy + 2][hx][V_U1] - R[hy - 2][hx][V_U1]));
+          } else if (hk[j] == 2) {
+            (&sm.s1buf[sbe][0][0])[hdst[j]] = mad(c.c1[0], R[hy][hx + 1][V_U0] - R[hy][hx - 1][V_U0],
+                                                  -c.c2[0] * (R[hy][hx + 2][V_U0] - R[hy][hx - 2][V_U0]));
+          }
+        }
       }
     }
     if (it < 4) continue;  // ring not yet full; slots written so far are not read again before the next sync
@@ -865,8 +1009,17 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
     };
 
     // --------------------------------------------------------------- phase 2b
-    // s_0 and s_1 on the centre plane's tile and halo.
-    {
+    // binary64 / double-float: s_0 and s_1 on the centre plane's tile and
+    // halo; binary32 has its helpers already (phase 2a of the plane's entry)
+    // and needs only the centre's in-plane gradients.
+    if constexpr (MIXZ) {
+      if constexpr (ZT) {
+        tmem_load_diag(twin, scen, g00c, g11c);
+      } else {
+        g00c = sm.dring[scen][0][ty][tx];
+        g11c = sm.dring[scen][1][ty][tx];
+      }
+    } else {
       const int sy = ty + HALO, sx = tx + HALO;
       auto u2at = [&](int slot, int yy, int xx) {
         if constexpr (ZT)
@@ -885,8 +1038,8 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         g00c = sm.dring[scen][0][ty][tx];
         g11c = sm.dring[scen][1][ty][tx];
       }
-      sm.s0buf[ty][sx] = g11c + d22;
-      sm.s1buf[sy][tx] = g00c + d22;
+      sm.s0buf[0][ty][sx] = g11c + d22;
+      sm.s1buf[0][sy][tx] = g00c + d22;
       const T(*R)[SX][NV] = sm.ring[fc];
 #pragma unroll
       for (int j = 0; j < HPT; ++j) {
@@ -894,15 +1047,15 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         if (hk[j] == 1) {
           const T d11 = mad(c.c1[1], R[hy + 1][hx][V_U1] - R[hy - 1][hx][V_U1],
                             -c.c2[1] * (R[hy + 2][hx][V_U1] - R[hy - 2][hx][V_U1]));
-          (&sm.s0buf[0][0])[hdst[j]] = d11 + u2z(hy, hx);
+          (&sm.s0buf[0][0][0])[hdst[j]] = d11 + u2z(hy, hx);
         } else if (hk[j] == 2) {
           const T d00 = mad(c.c1[0], R[hy][hx + 1][V_U0] - R[hy][hx - 1][V_U0],
                             -c.c2[0] * (R[hy][hx + 2][V_U0] - R[hy][hx - 2][V_U0]));
-          (&sm.s1buf[0][0])[hdst[j]] = d00 + u2z(hy, hx);
+          (&sm.s1buf[0][0][0])[hdst[j]] = d00 + u2z(hy, hx);
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
     // ---------------------------------------------------------------- phase 3
     {
       fetch_acc();
@@ -931,16 +1084,17 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       t.g[2][2] = d22;
 
       // x0 group first (SN2 ordering), then x1, x2
+      const int sbc = MIXZ ? rb[0] : 0;  // helper buffers of the centre plane
       {
         const int off[4] = {-2, -1, 1, 2};
         auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy][sx + off[k]][0], r); };
-        auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[ty][sx + off[k]]; };
+        auto sf = [&](int k, const T(&)[NV]) { return sm.s0buf[sbc][ty][sx + off[k]]; };
         axis_terms_any<0>(ld, sf, c, uc, t);
       }
       {
         const int off[4] = {-2, -1, 1, 2};
         auto ld = [&](int k, T(&r)[NV]) { load_rec(&C[sy + off[k]][sx][0], r); };
-        auto sf = [&](int k, const T(&)[NV]) { return sm.s1buf[sy + off[k]][tx]; };
+        auto sf = [&](int k, const T(&)[NV]) { return sm.s1buf[sbc][sy + off[k]][tx]; };
         axis_terms_any<1>(ld, sf, c, uc, t);
       }
       {
@@ -960,7 +1114,18 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
             return sm.dring[zs[k]][0][ty][tx] + sm.dring[zs[k]][1][ty][tx];
           }
         };
-        axis_terms_any<2>(ld, sf, c, uc, t);
+        // binary32: D1_x u2 and D1_y u2 of the x2 neighbours
+        auto xf = [&](int k, T& d02, T& d12) {
+          if constexpr (MIXZ) {
+            if constexpr (ZT) {
+              tmem_load_xdiag(twin2, zs[k], d02, d12);
+            } else {
+              d02 = sm.dring[zs[k]][2][ty][tx];
+              d12 = sm.dring[zs[k]][3][ty][tx];
+            }
+          }
+        };
+        axis_terms_any<2, MIXZ>(ld, sf, c, uc, t, xf);
       }
 
       const T rho = T(1) + rho_p;
@@ -1116,17 +1281,18 @@ __global__ void __launch_bounds__(TX* TY, fused_min_blocks<T, TY, ZT>())
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, TY, ZT>& sm = *reinterpret_cast<FusedSmem<T, TY, ZT>*>(smem_raw);
   constexpr int NCOL = tmem_columns<TY, T>();  // TX*TY/32 = TY warps
-  uint32_t tbase = 0;
-  if (ZT) tbase = tmem_acquire<NCOL>(&sm.tmem_base);
+  constexpr int NCOL2 = tmem_columns2<TY, T>();
+  uint32_t tbase = 0, tbase2 = 0;
+  if (ZT) tmem_acquire<NCOL, NCOL2>(sm.tmem_base, tbase, tbase2);
   double ke = 0.0, ens = 0.0;
   const int zbeg = blockIdx.z * a.zc;
   fused_march<T, TIN, TOUT, TY, RHS_ONLY, WITH_KE, DF, ZT>(a, c, blockIdx.x, blockIdx.y, zbeg, zbeg + a.zc, sm, ke,
-                                                          ens, tbase);
+                                                          ens, tbase, tbase2);
   if (WITH_KE) {
     const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     block_reduce_pair<TX * TY>(sm.red, ke, ens, a.ke_partials + 2 * b);
   }
-  if (ZT) tmem_release<NCOL>(tbase);
+  if (ZT) tmem_release<NCOL, NCOL2>(tbase, tbase2);
 }
 
 template <int TY, int W = TX>
