@@ -80,6 +80,7 @@ constexpr int NSLOT = 5;
 // skew form, so the factor 2 is applied once per point instead of once per
 // stencil neighbour; scaling by 2 is exact)
 enum { V_RHO, V_M0, V_M1, V_M2, V_E, V_U0, V_U1, V_U2, V_P, V_T, NV };
+static_assert(V_U2 == V_U1 + 1 && V_U1 % 2 == 0, "u1, u2 form one 8-byte pair of a binary32 record");
 
 // ZT (binary32 with the TMEM z queue): the x2 neighbours of a thread's own
 // column come from tensor memory, so shared memory keeps full records only
@@ -935,8 +936,24 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
       const int sy = ty + HALO, sx = tx + HALO;
       const T d00 = mad(c.c1[0], R[sy][sx + 1][V_U0] - R[sy][sx - 1][V_U0],
                         -c.c2[0] * (R[sy][sx + 2][V_U0] - R[sy][sx - 2][V_U0]));
-      const T d11 = mad(c.c1[1], R[sy + 1][sx][V_U1] - R[sy - 1][sx][V_U1],
-                        -c.c2[1] * (R[sy + 2][sx][V_U1] - R[sy - 2][sx][V_U1]));
+      // u1 and u2 of the x1 neighbours (adjacent fields: one 8-byte load each
+      // in binary32, whose records sit at 8-byte multiples)
+      T y1[4], y2[4];
+      {
+        const int oy[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if constexpr (std::is_same<T, float>::value && MIXZ) {
+            const float2 v = *reinterpret_cast<const float2*>(&R[sy + oy[k]][sx][V_U1]);
+            y1[k] = v.x;
+            y2[k] = v.y;
+          } else {
+            y1[k] = R[sy + oy[k]][sx][V_U1];
+            y2[k] = R[sy + oy[k]][sx][V_U2];
+          }
+        }
+      }
+      const T d11 = mad(c.c1[1], y1[2] - y1[1], -c.c2[1] * (y1[3] - y1[0]));
       if constexpr (ZT) {
         tmem_store_diag(twin, se, d00, d11);  // this thread's column only
       } else {
@@ -950,8 +967,7 @@ __device__ __forceinline__ void fused_march(const StageArgs& a, const Coef<T>& c
         // entering plane, read when it becomes the centre
         const T d02 = mad(c.c1[0], R[sy][sx + 1][V_U2] - R[sy][sx - 1][V_U2],
                           -c.c2[0] * (R[sy][sx + 2][V_U2] - R[sy][sx - 2][V_U2]));
-        const T d12 = mad(c.c1[1], R[sy + 1][sx][V_U2] - R[sy - 1][sx][V_U2],
-                          -c.c2[1] * (R[sy + 2][sx][V_U2] - R[sy - 2][sx][V_U2]));
+        const T d12 = mad(c.c1[1], y2[2] - y2[1], -c.c2[1] * (y2[3] - y2[0]));
         if constexpr (ZT) {
           tmem_store_xdiag(twin2, se, d02, d12);
         } else {
