@@ -58,16 +58,16 @@ ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0, "fp32df": 320.0 / 3.0, "d
 # once the sources differ.
 #   fp64 flop_per_pt: binary64 flop executed (2 DFMA + DADD + DMUL), mean of
 #        the three stages of a 256^3 step; traffic_per_pt: DRAM read + write
-#        bytes per point of one launch, same capture (2.2503e9 per launch at
+#        bytes per point of one launch, same capture (2.2499e9 per launch at
 #        256^3; scaled by points to other grids);
 #   df64 inst_per_pt: thread instructions (smsp__inst_executed x 32 / points),
 #        mean of the three stages of a 256^3 step, per z-queue mode.
 KERNEL_SOURCES = ["fused_stage.cuh", "fused_fp64.cu", "fused_df64.cu", "dfloat.cuh", "fpconv.cuh", "f32x2.cuh",
                   "sbli_internal.cuh"]
 KERNEL_COUNTS = {
-    "fp64": {"flop_per_pt": 572.02, "traffic_per_pt": 2.2503e9 / 256**3, "sources": "fb3e2bfdb068",
+    "fp64": {"flop_per_pt": 568.44, "traffic_per_pt": 2.2499e9 / 256**3, "sources": "651ecf03b0a6",
              "profile": "profiles/fused_stage_fp64_256.md"},
-    "df64": {"inst_per_pt": {0: 3727.1, 1: 3693.1}, "sources": "fb3e2bfdb068",
+    "df64": {"inst_per_pt": {0: 3727.1, 1: 3693.1}, "sources": "651ecf03b0a6",
              "profile": "profiles/fused_stage_df64_256.md"},
 }
 

@@ -120,10 +120,11 @@ struct FusedSmem {
   uint32_t tmem_base[2];      // TMEM allocations (z queue variant)
 };
 
-// 1/rho for the primitives (Eqs. 4-5): correctly rounded in binary64 and
-// double-float; binary32 takes the hardware approximation (rcp.approx,
-// within one unit in the last place), far inside the binary32 tolerance and
-// one instruction instead of the rounding-correction sequence.
+// 1/rho for the primitives (Eqs. 4-5): a Newton-refined approximation in
+// binary64, a double-word reciprocal in double-float; binary32 takes the
+// hardware approximation (rcp.approx, within one unit in the last place),
+// far inside the binary32 tolerance and one instruction instead of the
+// rounding-correction sequence.
 __device__ __forceinline__ float rcp_approx_f32(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -131,8 +132,20 @@ __device__ __forceinline__ float rcp_approx_f32(float x) {
 }
 template <typename T>
 __device__ __forceinline__ T recip(T x);
+// binary64: the hardware approximation (rcp.approx.ftz.f64) refined by two
+// Newton-Raphson steps y <- y + y (1 - x y), each a pair of fused
+// multiply-adds that squares the relative error (within one unit in the
+// last place of 1/x; tests/test_gpu_recip.py compares it with CUDA's
+// correctly rounded reciprocal)
 template <>
-__device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ double recip<double>(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
 template <>
 __device__ __forceinline__ float recip<float>(float x) { return rcp_approx_f32(x); }
 template <>
