@@ -13,7 +13,8 @@ The JSON line carries:
                sides; max over ranks);
   e2e          the same metric through the public C ABI with host buffers:
                every e2e step copies the initial state from pinned host
-               memory, runs --solve-steps time steps, copies the state back;
+               memory, runs --solve-steps time steps, copies the state back
+               (mean of --e2e-reps steps after one untimed);
   roofline     the fused stage kernel against its binding roofline: the FP64
                pipe for binary64, whose peak is measured in the same run by
                the library's FMA-throughput probe (clocks sampled meanwhile);
@@ -106,7 +107,7 @@ def parse():
     ap.add_argument("--dt", type=float, default=None,
                     help="time step (default 5e-4 for n >= 512, the linear stability limit there, else 1e-3)")
     ap.add_argument("--solve-steps", type=int, default=10, help="time steps per e2e solve")
-    ap.add_argument("--e2e-reps", type=int, default=2)
+    ap.add_argument("--e2e-reps", type=int, default=3, help="timed e2e solves (mean), after one untimed")
     ap.add_argument("--no-legs", action="store_true", help="skip the FP32 512^3 and store-all legs")
     ap.add_argument("--leg-steps", type=int, default=200, help="time steps of the 512^3 binary32 legs")
     ap.add_argument("--df64-leg-steps", type=int, default=40)
@@ -650,7 +651,7 @@ def run_ours(args):
     g.init_tgv(1.0)
     g.get_state(q_host)
     e2e_t = []
-    for _ in range(args.e2e_reps):
+    for rep in range(1 + args.e2e_reps):  # the first, untimed, touches the pinned buffers and graphs once
         dist_barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -658,8 +659,9 @@ def run_ours(args):
         S.sbli_step_n(g.handle, args.solve_steps, dt)
         S.sbli_get_state(g.handle, r_host.data_ptr(), True)
         torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t0)
-    t_e2e = dist_max(min(e2e_t))
+        if rep > 0:
+            e2e_t.append(time.perf_counter() - t0)
+    t_e2e = dist_max(sum(e2e_t) / len(e2e_t))
     state_bytes = 5 * P * 8
     g.close()
     del g, q_host, r_host
@@ -719,7 +721,8 @@ def run_ours(args):
                    "launch_config_fields": "tile_y, planes_per_cta, z_queue, columns_per_thread"},
         "e2e": {"value": 3.0 * P * args.solve_steps * ws / t_e2e, "unit": "pt-stage/s",
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-                "note": f"each e2e step = H2D state + {args.solve_steps} time steps + D2H state"},
+                "note": f"each e2e step = H2D state + {args.solve_steps} time steps + D2H state; mean of "
+                        f"{args.e2e_reps} after one untimed"},
         "roofline": roof,
         "fp64_peak_probe": {"tflops": fp64_probe["flop_per_s"] / 1e12, "ms": fp64_probe["ms"],
                             "clocks": fp64_probe["clocks"]},
